@@ -1,0 +1,273 @@
+/*
+ * rdct.h -- C-ABI of librdct, a GB300 (sm_103a) library for the block image
+ * codec built on the round-off DCT approximation of Cintra & Bayer, "A DCT
+ * Approximation for Image Compression".
+ *
+ * The method (Sec. 2-3 of the paper):
+ *   C0 = [2C]      the 8-point DCT matrix scaled by 2 and rounded (entries 0, +-1)
+ *   S  = sqrt((C0 C0^T)^-1) = diag(1/(2 sqrt2), 1/sqrt6, 1/2, 1/sqrt6, ...)
+ *   C_orth = S C0  (orthogonal)
+ *   per 8x8 block A:  Y = C0 A C0^T  (additions only)
+ *                     Yhat = first r zigzag coefficients of S Y S (S folded
+ *                            into the compression step), the rest zeroed
+ *                     Xhat = C_orth^T Yhat C_orth = C0^T S Yhat S C0
+ *   quality: SSE / MSE / PSNR of Xhat against A.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an rdct_status; no C++ exception crosses this ABI.
+ *     rdct_status_string() names a status; rdct_last_error() copies the
+ *     calling thread's last detailed message.
+ *   - Data pointers are DEVICE pointers owned by the caller unless a
+ *     parameter says "host".  The library never frees caller memory.
+ *   - Calls that take an rdct_stream (a cudaStream_t; NULL = legacy default
+ *     stream) are asynchronous on that stream.  Arguments are validated
+ *     synchronously before anything is launched (RDCT_ERR_ARG /
+ *     RDCT_ERR_SHAPE with nothing enqueued).  Errors raised by a kernel
+ *     surface as RDCT_ERR_CUDA from this or a later call, or from rdct_sync.
+ *   - Planes are 8-bit, row-major, with a pitch in bytes >= width.  Width
+ *     and height must be positive multiples of 8 (the paper's images are
+ *     512 x 512; other sizes are rejected, RDCT_ERR_SHAPE).  Multi-channel
+ *     images are passed as separate planes.
+ *   - Coefficient blocks are block-major: block (by, bx) of a plane with
+ *     nbw = w/8 blocks per row is block index by * nbw + bx; within a block
+ *     the 64 values are row-major (row = vertical frequency).
+ *   - Zigzag order is the JPEG scan (first step horizontal): (0,0), (0,1),
+ *     (1,0), (2,0), (1,1), (0,2), ...  This is the reading taken of the
+ *     paper's "standard zigzag sequence" (Sec. 3).
+ *   - Rounding to 8 bits: clamp(round(x), 0, 255), nearest integer; the
+ *     integer path of rdct_fused rounds exact halves upward, the others
+ *     round them to even.  Results may differ by 1 at exact halves.
+ */
+#ifndef RDCT_H
+#define RDCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(RDCT_BUILD) && defined(__GNUC__)
+#define RDCT_API __attribute__((visibility("default")))
+#else
+#define RDCT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RDCT_OK = 0,
+    RDCT_ERR_ARG = 1,        /* bad pointer, count or parameter */
+    RDCT_ERR_SHAPE = 2,      /* width/height not a positive multiple of 8, pitch < width */
+    RDCT_ERR_OOM = 3,        /* a device or pinned-host allocation failed */
+    RDCT_ERR_TOO_LARGE = 4,  /* request larger than a configured budget or limit */
+    RDCT_ERR_CUDA = 5,       /* a CUDA runtime call or kernel failed */
+    RDCT_ERR_TIMEOUT = 6,    /* a wait ran out before the work completed */
+    RDCT_ERR_BUSY = 7,       /* queue full; retry later */
+    RDCT_ERR_NOT_FOUND = 8,  /* unknown ticket or handle */
+    RDCT_ERR_CANCELLED = 9   /* the request was cancelled before it ran */
+} rdct_status;
+
+/* Which orthonormal transform a call applies (Sec. 2-3). */
+typedef enum {
+    RDCT_KIND_RDCT = 0, /* the proposed C_orth = S C0 (integer butterflies + folded scaling) */
+    RDCT_KIND_DCT = 1   /* the exact 8-point DCT (FP32), the paper's comparison baseline */
+} rdct_kind;
+
+typedef void *rdct_stream; /* a cudaStream_t */
+
+/* One 8-bit plane in device memory. */
+typedef struct {
+    const uint8_t *ptr; /* first pixel */
+    int64_t pitch;      /* bytes between rows, >= w */
+    int32_t w, h;       /* pixels; positive multiples of 8 */
+} rdct_plane;
+
+/* Reconstruction destination (device).  Either pointer may be NULL.
+ * u8 has pitch `pitch` bytes; f32 has pitch `pitch_f32` floats. */
+typedef struct {
+    uint8_t *u8;
+    float *f32;
+    int64_t pitch;
+    int64_t pitch_f32;
+} rdct_out;
+
+/* ---------------------------------------------------------------- basics */
+
+RDCT_API const char *rdct_status_string(rdct_status s);
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to cap bytes); returns its full length. */
+RDCT_API size_t rdct_last_error(char *buf, size_t cap);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+RDCT_API int32_t rdct_version(void);
+/* Blocks the host until all work on `stream` is done; reports async errors. */
+RDCT_API rdct_status rdct_sync(rdct_stream stream);
+
+/* ------------------------------------------------------- the method's steps */
+
+/* Forward transform Y = C0 A C0^T for every 8x8 block A of `src`
+ * (Sec. 3 with T = C0; C0 from Sec. 2).  Y: int32, block-major,
+ * (w/8)*(h/8)*64 values.  |Y| <= 16320, exact (additions only). */
+RDCT_API rdct_status rdct_forward(const rdct_plane *src, int32_t *Y, rdct_stream stream);
+
+/* Orthonormal forward coefficients in FP32, block-major [blocks][64]:
+ * kind RDCT gives S Y S = C_orth A C_orth^T (Sec. 2), kind DCT gives C A C^T. */
+RDCT_API rdct_status rdct_forward_f32(const rdct_plane *src, rdct_kind kind, float *Y, rdct_stream stream);
+
+/* Compression (Sec. 2 "scaling merged into the quantization", Sec. 3 zonal
+ * truncation): for each of `nblocks` blocks of int32 Y (block-major, 64
+ * each), write the first r zigzag coefficients of S Y S as FP32, packed
+ * [nblocks][r].  1 <= r <= 64. */
+RDCT_API rdct_status rdct_compress(const int32_t *Y, int64_t nblocks, int32_t r, float *Yc, rdct_stream stream);
+
+/* Inverse (Sec. 3 "inverse procedure", Sec. 2 orthogonality): from packed
+ * [nbw*nbh][r] zigzag coefficients Yc, reconstruct Xhat = M^T Yhat M per
+ * block (M = C_orth for kind RDCT, C for kind DCT; positions past r are
+ * zero), writing FP32 and/or clamped rounded uint8 pixels into `out`
+ * (an image of 8*nbw x 8*nbh pixels). */
+RDCT_API rdct_status rdct_inverse(const float *Yc, int64_t nbw, int64_t nbh, int32_t r, rdct_kind kind,
+                         const rdct_out *out, rdct_stream stream);
+
+/* Quality (Sec. 3): MSE and PSNR = 10 log10(255^2 / MSE) of a reconstruction
+ * against the reference plane.  rec->u8 is used when non-NULL, else
+ * rec->f32.  mse and psnr are DEVICE pointers to one double each; PSNR is
+ * +inf when MSE is 0.  Uses a small stream-ordered scratch allocation. */
+RDCT_API rdct_status rdct_mse_psnr(const rdct_plane *ref, const rdct_out *rec, double *mse, double *psnr,
+                          rdct_stream stream);
+
+/* The whole path in one kernel (Sec. 3): forward, keep r zigzag
+ * coefficients with the S scaling, inverse, squared error.  `out` may be
+ * NULL (error only).  *sse (DEVICE double) receives the sum over pixels of
+ * (Xhat - A)^2 for the unrounded reconstruction; for kind RDCT it is exact
+ * (integer arithmetic, 576 * SSE accumulated in 64 bits). */
+RDCT_API rdct_status rdct_fused(const rdct_plane *src, int32_t r, rdct_kind kind, const rdct_out *out, double *sse,
+                       rdct_stream stream);
+
+/* The r sweep of Sec. 3 in one pass per plane: sse_by_r (DEVICE, [n][64]
+ * doubles) receives, for each plane i and r = 1..64, the squared error of
+ * the reconstruction keeping r coefficients, computed from the per-zigzag-
+ * position energy of the orthonormal coefficients (Parseval: the transform
+ * is orthogonal).  Exact for kind RDCT; FP32 products, FP64 sums for DCT. */
+RDCT_API rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r, rdct_stream stream);
+
+/* ------------------------------------------------ batches of uneven planes */
+
+/* One plane of a batch.  SSE is summed per image over its planes. */
+typedef struct {
+    rdct_plane src;
+    uint8_t *dst;      /* uint8 reconstruction (device) or NULL */
+    int64_t dst_pitch; /* bytes, >= src.w when dst != NULL */
+    int32_t r;         /* 1..64 */
+    int32_t image;     /* 0 <= image < nimages */
+} rdct_job;
+
+/* Launch shape of the persistent fused kernel. */
+typedef struct {
+    int32_t warps_per_cta;   /* 1..8 */
+    int32_t ctas_per_sm;     /* grid = ctas_per_sm * SM count */
+    int32_t items_per_chunk; /* strips handed to a warp at a time */
+    int32_t blocks_per_thread; /* 1 or 2 horizontally adjacent 8x8 blocks per thread */
+} rdct_tune;
+
+typedef struct rdct_plan rdct_plan;
+
+/* Build a plan over `njobs` planes: a flattened index of 8-row strips over
+ * all planes, grouped into chunks (one descriptor per chunk), uploaded to
+ * the device once.  tune may be NULL (defaults / autotune cache).  All job
+ * pointers must stay valid while the plan is used. */
+RDCT_API rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t nimages, const rdct_tune *tune,
+                                   rdct_plan **plan);
+/* Run the whole batch as ONE persistent launch; the launch sequence is
+ * captured into a CUDA graph on the first run on a given stream and replayed
+ * afterwards.  sse_per_image: DEVICE, [nimages] doubles, overwritten. */
+RDCT_API rdct_status rdct_batch_run(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
+/* Same work with one plain launch per plane (the baseline batching is
+ * compared against). */
+RDCT_API rdct_status rdct_batch_run_per_plane(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
+RDCT_API rdct_status rdct_batch_plan_get_tune(const rdct_plan *plan, rdct_tune *tune);
+RDCT_API rdct_status rdct_batch_plan_destroy(rdct_plan *plan);
+
+/* Time candidate launch shapes on this batch (CUDA events, repeated runs)
+ * and return the fastest in *best; the result is also kept in a per-process
+ * cache keyed by the batch's shape class. */
+RDCT_API rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, rdct_tune *best, rdct_stream stream);
+
+/* -------------------------------------------- host-resident streaming path */
+
+/* One plane in HOST memory (pinned or pageable) for the streaming calls. */
+typedef struct {
+    const uint8_t *src; /* host */
+    uint8_t *dst;       /* host, may be NULL */
+    int64_t pitch;      /* bytes, for both src and dst */
+    int32_t w, h;
+    int32_t r;
+    int32_t image;
+} rdct_host_job;
+
+typedef struct rdct_pipeline rdct_pipeline;
+
+/* A copy/compute pipeline with `device_budget_bytes` of staging memory split
+ * into `depth` slots: host->device copies, kernels and device->host copies
+ * of consecutive groups of planes overlap on separate streams. */
+RDCT_API rdct_status rdct_pipeline_create(int64_t device_budget_bytes, int32_t depth, rdct_pipeline **pipe);
+/* Process planes that live in host memory: copy in, run the fused path,
+ * copy the uint8 reconstructions back, and write per-image SSE to the HOST
+ * array sse_per_image[nimages].  Returns when everything is done. */
+RDCT_API rdct_status rdct_pipeline_run(rdct_pipeline *pipe, const rdct_host_job *jobs, int32_t njobs, int32_t nimages,
+                              double *sse_per_image);
+RDCT_API rdct_status rdct_pipeline_destroy(rdct_pipeline *pipe);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct {
+    int64_t device_budget_bytes; /* admission limit for resident request buffers */
+    int32_t max_batch;           /* requests per launch, >= 1 */
+    int32_t queue_capacity;      /* pending requests before submit returns BUSY */
+    int32_t streams;             /* launches in flight, >= 1 */
+    int32_t max_wait_us;         /* how long a lone request may wait for company */
+} rdct_server_opts;
+
+/* A request: an image of `planes` planes (1 or 3), all w x h, packed
+ * contiguously in host memory (plane p at src + p*pitch*h). */
+typedef struct {
+    const uint8_t *src; /* host */
+    uint8_t *dst;       /* host, receives the uint8 reconstruction (same layout), may be NULL */
+    int64_t pitch;
+    int32_t w, h, planes, r;
+} rdct_request;
+
+typedef struct {
+    rdct_status status;
+    double sse;        /* summed over planes, unrounded reconstruction */
+    double mse, psnr;  /* over all samples of the image */
+    double latency_us; /* submit -> completion */
+} rdct_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches;
+    double p50_us, p99_us, mean_us;
+    double gpixels_per_s; /* samples processed / busy wall time */
+    int64_t peak_resident_bytes;
+} rdct_server_stats;
+
+typedef struct rdct_server rdct_server;
+
+RDCT_API rdct_status rdct_server_create(const rdct_server_opts *opts, rdct_server **server);
+/* Queue a request (host buffers must stay valid until it completes).
+ * RDCT_ERR_BUSY if the queue is full, RDCT_ERR_TOO_LARGE if it can never fit
+ * the budget. */
+RDCT_API rdct_status rdct_server_submit(rdct_server *server, const rdct_request *req, uint64_t *ticket);
+/* Wait up to timeout_us (negative = forever) for a ticket.  RDCT_ERR_TIMEOUT
+ * leaves it pending; on success the ticket is retired. */
+RDCT_API rdct_status rdct_server_wait(rdct_server *server, uint64_t ticket, int64_t timeout_us, rdct_result *result);
+/* Non-blocking: RDCT_OK and the result if done, RDCT_ERR_BUSY if pending. */
+RDCT_API rdct_status rdct_server_poll(rdct_server *server, uint64_t ticket, rdct_result *result);
+/* Cancel a request that has not been admitted to the device yet. */
+RDCT_API rdct_status rdct_server_cancel(rdct_server *server, uint64_t ticket);
+RDCT_API rdct_status rdct_server_stats_get(rdct_server *server, rdct_server_stats *stats);
+/* Drains outstanding work, then frees everything. */
+RDCT_API rdct_status rdct_server_destroy(rdct_server *server);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RDCT_H */

@@ -1,0 +1,311 @@
+// rdct_batch.cu -- batches of uneven planes in one graph launch, and the
+// autotuner that picks the launch shape.
+//
+// The paper runs its experiment image by image (Sec. 3).  Here every plane of
+// a batch is cut into strips (one block row, 32 blocks wide), strips are
+// grouped into chunks, and the chunk table is walked by persistent warps, so a
+// batch of thousands of planes of different sizes and r costs one graph
+// launch.  The retained-coefficient count r varies per plane; chunks are
+// ordered by the anti-diagonal class of r so that neighbouring warps run the
+// same specialised code.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rdct_device.cuh"
+#include "rdct_internal.h"
+
+using namespace rdct;
+
+struct rdct_plan {
+    int device = 0;
+    int32_t nimages = 0;
+    rdct_tune tune{};
+    std::vector<JobDesc> jobs;     // host copy, segs computed for the plan's tile
+    std::vector<JobDesc> jobs_pp;  // per-plane launches (one block per thread)
+    std::vector<Chunk> chunks;
+    int32_t class_begin[kBatchClasses + 1] = {0};
+    JobDesc *d_jobs = nullptr;
+    Chunk *d_chunks = nullptr;
+    // graph cache: one executable per (sse pointer)
+    std::mutex mu;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double *exec_sse = nullptr;
+};
+
+namespace {
+
+rdct_tune default_tune() {
+    rdct_tune t{};
+    t.warps_per_cta = 8;
+    t.ctas_per_sm = 0;  // occupancy limit
+    t.items_per_chunk = 8;
+    t.blocks_per_thread = 1;
+    return t;
+}
+
+rdct_status validate_tune(const rdct_tune &t) {
+    if (t.warps_per_cta < 1 || t.warps_per_cta > 8 || t.ctas_per_sm < 0 || t.ctas_per_sm > 64 ||
+        t.items_per_chunk < 1 || t.items_per_chunk > 4096 || t.blocks_per_thread != 1)
+        return set_error(RDCT_ERR_ARG, "rdct_tune: out of range (warps 1..8, ctas_per_sm 0..64, "
+                                       "items_per_chunk 1..4096, blocks_per_thread 1)");
+    return RDCT_OK;
+}
+
+rdct_status validate_jobs(const rdct_job *jobs, int32_t njobs, int32_t nimages) {
+    if (!jobs && njobs > 0) return set_error(RDCT_ERR_ARG, "batch: null job array");
+    if (njobs < 0 || nimages < 0) return set_error(RDCT_ERR_ARG, "batch: negative count");
+    for (int32_t i = 0; i < njobs; ++i) {
+        const rdct_job &j = jobs[i];
+        rdct_status st = validate_plane(&j.src, "batch job");
+        if (st) return set_error(st, "job " + std::to_string(i) + ": " + std::string(""));
+        if (j.r < 1 || j.r > 64) return set_error(RDCT_ERR_ARG, "job " + std::to_string(i) + ": r must be in 1..64");
+        if (j.image < 0 || j.image >= nimages)
+            return set_error(RDCT_ERR_ARG, "job " + std::to_string(i) + ": image index out of range");
+        if (j.dst && j.dst_pitch < j.src.w)
+            return set_error(RDCT_ERR_SHAPE, "job " + std::to_string(i) + ": dst pitch smaller than width");
+    }
+    return RDCT_OK;
+}
+
+void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
+    const int bpt = p->tune.blocks_per_thread;
+    p->jobs.resize(njobs);
+    p->jobs_pp.resize(njobs);
+    for (int32_t i = 0; i < njobs; ++i) {
+        const rdct_job &j = jobs[i];
+        p->jobs[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, bpt);
+        p->jobs_pp[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, 1);
+    }
+    std::vector<Chunk> ch;
+    const int per = p->tune.items_per_chunk;
+    for (int32_t i = 0; i < njobs; ++i) {
+        const int items = p->jobs[i].nbh * p->jobs[i].segs;
+        const int d = diag_class_host(p->jobs[i].r);
+        for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), d});
+    }
+    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) {
+        const int ca = batch_class_of_diag(a.diag), cb = batch_class_of_diag(b.diag);
+        if (ca != cb) return ca < cb;
+        return a.diag < b.diag;
+    });
+    p->chunks = std::move(ch);
+    for (int c = 0; c <= kBatchClasses; ++c) p->class_begin[c] = 0;
+    for (const Chunk &c : p->chunks) p->class_begin[batch_class_of_diag(c.diag) + 1]++;
+    for (int c = 0; c < kBatchClasses; ++c) p->class_begin[c + 1] += p->class_begin[c];
+}
+
+cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
+    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c) {
+        const int32_t b = p->class_begin[c], n = p->class_begin[c + 1] - b;
+        if (n > 0)
+            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, c, p->tune.ctas_per_sm, p->tune.warps_per_cta,
+                                   s);
+    }
+    if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
+    return e;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, rdct_tune> g_tune_cache;
+
+std::string shape_key(const rdct_job *jobs, int32_t njobs) {
+    // shape class: job count, total blocks (log2 bucket) and blocks per r class
+    int64_t blocks = 0;
+    int64_t per_class[kBatchClasses] = {0};
+    for (int32_t i = 0; i < njobs; ++i) {
+        const int64_t b = (int64_t)(jobs[i].src.w / 8) * (jobs[i].src.h / 8);
+        blocks += b;
+        per_class[batch_class_of_diag(diag_class_host(jobs[i].r))] += b;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string k = "dev" + std::to_string(dev) + ":n" + std::to_string(njobs);
+    int lg = 0;
+    while ((int64_t)1 << (lg + 1) <= blocks) ++lg;
+    k += ":b" + std::to_string(lg);
+    for (int c = 0; c < kBatchClasses; ++c) k += ":" + std::to_string(blocks ? (int)(10 * per_class[c] / blocks) : 0);
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t nimages, const rdct_tune *tune,
+                                   rdct_plan **plan) {
+    if (!plan) return set_error(RDCT_ERR_ARG, "rdct_batch_plan_create: null plan");
+    *plan = nullptr;
+    rdct_status st = validate_jobs(jobs, njobs, nimages);
+    if (st) return st;
+    rdct_tune t = default_tune();
+    if (tune) {
+        t = *tune;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(shape_key(jobs, njobs));
+        if (it != g_tune_cache.end()) t = it->second;
+    }
+    st = validate_tune(t);
+    if (st) return st;
+    rdct_plan *p = new (std::nothrow) rdct_plan();
+    if (!p) return set_error(RDCT_ERR_OOM, "rdct_batch_plan_create: host allocation failed");
+    p->nimages = nimages;
+    p->tune = t;
+    cudaGetDevice(&p->device);
+    build_tables(p, jobs, njobs);
+    const size_t jb = p->jobs.size() * sizeof(JobDesc), cb = p->chunks.size() * sizeof(Chunk);
+    cudaError_t e = cudaSuccess;
+    if (jb) e = cudaMalloc(&p->d_jobs, jb);
+    if (e == cudaSuccess && cb) e = cudaMalloc(&p->d_chunks, cb);
+    if (e != cudaSuccess) {
+        rdct_batch_plan_destroy(p);
+        return set_error(RDCT_ERR_OOM, "rdct_batch_plan_create: device table allocation failed");
+    }
+    if (jb) e = cudaMemcpy(p->d_jobs, p->jobs.data(), jb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && cb) e = cudaMemcpy(p->d_chunks, p->chunks.data(), cb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        rdct_batch_plan_destroy(p);
+        return cuda_error(e, "rdct_batch_plan_create");
+    }
+    *plan = p;
+    return RDCT_OK;
+}
+
+rdct_status rdct_batch_run(rdct_plan *p, double *sse, rdct_stream stream) {
+    if (!p || !sse) return set_error(RDCT_ERR_ARG, "rdct_batch_run: null argument");
+    if (reinterpret_cast<uintptr_t>(sse) % 8) return set_error(RDCT_ERR_ARG, "rdct_batch_run: misaligned sse");
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (!p->exec || p->exec_sse != sse) {
+        if (p->exec) {
+            cudaGraphExecDestroy(p->exec);
+            p->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        RDCT_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_batch(p, sse, p->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_error(e, "rdct_batch_run: capture");
+        }
+        if (e2 != cudaSuccess) return cuda_error(e2, "rdct_batch_run: end capture");
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->exec = nullptr;
+            return cuda_error(e, "rdct_batch_run: instantiate");
+        }
+        p->exec_sse = sse;
+    }
+    RDCT_CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    return RDCT_OK;
+}
+
+rdct_status rdct_batch_run_per_plane(rdct_plan *p, double *sse, rdct_stream stream) {
+    if (!p || !sse) return set_error(RDCT_ERR_ARG, "rdct_batch_run_per_plane: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    RDCT_CUDA_TRY(cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s));
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
+    for (const JobDesc &j : p->jobs_pp) RDCT_CUDA_TRY(launch_fused_single(j, RDCT_KIND_RDCT, acc + j.image, 0, 8, s));
+    RDCT_CUDA_TRY(launch_sse576_to_double(sse, p->nimages, s));
+    return RDCT_OK;
+}
+
+rdct_status rdct_batch_plan_get_tune(const rdct_plan *p, rdct_tune *tune) {
+    if (!p || !tune) return set_error(RDCT_ERR_ARG, "rdct_batch_plan_get_tune: null argument");
+    *tune = p->tune;
+    return RDCT_OK;
+}
+
+rdct_status rdct_batch_plan_destroy(rdct_plan *p) {
+    if (!p) return RDCT_OK;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->cap_stream) {
+        cudaStreamSynchronize(p->cap_stream);
+        cudaStreamDestroy(p->cap_stream);
+    }
+    if (p->d_jobs) cudaFree(p->d_jobs);
+    if (p->d_chunks) cudaFree(p->d_chunks);
+    delete p;
+    return RDCT_OK;
+}
+
+rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, rdct_tune *best, rdct_stream stream) {
+    if (!best) return set_error(RDCT_ERR_ARG, "rdct_autotune: null result");
+    rdct_status st = validate_jobs(jobs, njobs, nimages);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *sse = nullptr;
+    if (cudaMalloc(&sse, (size_t)(nimages > 0 ? nimages : 1) * sizeof(double)) != cudaSuccess)
+        return set_error(RDCT_ERR_OOM, "rdct_autotune: scratch allocation failed");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<rdct_tune> cands;
+    for (int warps : {2, 4, 8})
+        for (int ctas : {0, 1, 2})
+            for (int items : {2, 4, 8, 16, 32}) {
+                rdct_tune t{};
+                t.warps_per_cta = warps;
+                t.ctas_per_sm = ctas;
+                t.items_per_chunk = items;
+                t.blocks_per_thread = 1;
+                cands.push_back(t);
+            }
+    float best_ms = 1e30f;
+    rdct_tune best_t = default_tune();
+    rdct_status result = RDCT_OK;
+    for (const rdct_tune &t : cands) {
+        rdct_plan *p = nullptr;
+        st = rdct_batch_plan_create(jobs, njobs, nimages, &t, &p);
+        if (st) {
+            result = st;
+            break;
+        }
+        float ms_sum = 0.0f;
+        bool ok = rdct_batch_run(p, sse, s) == RDCT_OK;  // capture + warm-up
+        const int reps = 3;
+        std::vector<float> times;
+        for (int k = 0; k < reps && ok; ++k) {
+            cudaEventRecord(e0, s);
+            ok = rdct_batch_run(p, sse, s) == RDCT_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            times.push_back(ms);
+            ms_sum += ms;
+        }
+        rdct_batch_plan_destroy(p);
+        if (!ok) {
+            result = set_error(RDCT_ERR_CUDA, "rdct_autotune: a candidate failed to run");
+            break;
+        }
+        std::sort(times.begin(), times.end());
+        const float med = times[times.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sse);
+    if (result != RDCT_OK) return result;
+    *best = best_t;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[shape_key(jobs, njobs)] = best_t;
+    return RDCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// rdct_fused.cu -- dispatch of the fused path (Sec. 3 of Cintra & Bayer:
+// forward, zonal truncation with the S scaling, inverse, squared error) and
+// the persistent batch kernels.
+#include "rdct_blocks.cuh"
+
+namespace rdct {
+
+cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps,
+                                cudaStream_t s) {
+    const int d = diag_class_host(job.r);
+    const int64_t items = (int64_t)job.nbh * job.segs;
+    const int out = (job.dst ? 1 : 0) | (job.dstf ? 2 : 0);
+    const DctConsts C = kind == RDCT_KIND_DCT ? make_dct_consts() : DctConsts{};
+#define RDCT_SINGLE(o, k) return launch_single_variant<o, k>(d, items, ctas_per_sm, warps, job, acc, C, s)
+    if (kind == RDCT_KIND_RDCT) {
+        switch (out) {
+            case 0: RDCT_SINGLE(0, RDCT_KIND_RDCT);
+            case 1: RDCT_SINGLE(1, RDCT_KIND_RDCT);
+            case 2: RDCT_SINGLE(2, RDCT_KIND_RDCT);
+            default: RDCT_SINGLE(3, RDCT_KIND_RDCT);
+        }
+    }
+    switch (out) {
+        case 0: RDCT_SINGLE(0, RDCT_KIND_DCT);
+        case 1: RDCT_SINGLE(1, RDCT_KIND_DCT);
+        case 2: RDCT_SINGLE(2, RDCT_KIND_DCT);
+        default: RDCT_SINGLE(3, RDCT_KIND_DCT);
+    }
+#undef RDCT_SINGLE
+}
+
+int batch_class_of_diag(int d) { return d <= 5 ? 0 : (d <= 8 ? 1 : 2); }
+
+cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
+                               int cls, int ctas_per_sm, int warps, cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    if (cls == 0) launch_persistent(fused_batch_kernel<1, 0, 5>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
+    else if (cls == 1) launch_persistent(fused_batch_kernel<1, 6, 8>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
+    else launch_persistent(fused_batch_kernel<1, 9, 14>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
+    return cudaGetLastError();
+}
+
+}  // namespace rdct

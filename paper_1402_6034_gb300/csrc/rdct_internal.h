@@ -1,0 +1,87 @@
+// rdct_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/rdct.h"
+
+namespace rdct {
+
+// One plane as the kernels see it (device descriptor).
+struct JobDesc {
+    const uint8_t *src;
+    uint8_t *dst;     // uint8 reconstruction or nullptr
+    float *dstf;      // FP32 reconstruction or nullptr
+    int64_t src_pitch, dst_pitch, dstf_pitch;  // bytes, bytes, floats
+    int32_t nbw, nbh; // blocks per row / per column
+    int32_t r;        // retained coefficients, 1..64
+    int32_t image;    // SSE slot
+    int32_t segs;     // strips per block row = ceil(nbw / (32 * blocks_per_thread))
+    int32_t align;    // 16 if src and src_pitch are 16-byte aligned, 8 if 8-byte, else 1
+    int32_t dalign;   // same for dst
+    int32_t pad;
+};
+
+// A run of consecutive strips of one job handed to one warp.
+struct Chunk {
+    int32_t job, item0, nitems, diag;
+};
+
+// FP32 constants of the exact DCT (host-computed from cos in double).
+struct DctConsts {
+    float c[64];  // C[k][n]
+};
+// FP32 d_i d_j products (orthonormal scaling of C0 coefficients).
+struct ScaleConsts {
+    float dd[64];
+};
+
+// Error state (thread-local message).
+rdct_status set_error(rdct_status s, const std::string &msg);
+rdct_status cuda_error(cudaError_t e, const char *what);
+#define RDCT_CUDA_TRY(expr)                                        \
+    do {                                                           \
+        cudaError_t e_ = (expr);                                   \
+        if (e_ != cudaSuccess) return ::rdct::cuda_error(e_, #expr); \
+    } while (0)
+
+DctConsts make_dct_consts();
+ScaleConsts make_scale_consts();
+int sm_count();
+rdct_status validate_plane(const rdct_plane *p, const char *what);
+JobDesc make_job(const rdct_plane &src, uint8_t *dst, int64_t dst_pitch, float *dstf, int64_t dstf_pitch, int32_t r,
+                 int32_t image, int bpt);
+int diag_class_host(int r);
+
+// ---------------------------------------------------------------- launchers
+// (all asynchronous on `s`; return cudaGetLastError of the launch)
+cudaError_t launch_forward(const JobDesc &job, int32_t *Y, cudaStream_t s);
+cudaError_t launch_forward_f32(const JobDesc &job, int kind, float *Y, cudaStream_t s);
+cudaError_t launch_compress(const int32_t *Y, int64_t nblocks, int32_t r, float *Yc, cudaStream_t s);
+cudaError_t launch_inverse(const float *Yc, int64_t nbw, int64_t nbh, int32_t r, int kind, uint8_t *u8,
+                           int64_t pitch, float *f32, int64_t pitch_f32, cudaStream_t s);
+// SSE of rec vs ref accumulated into acc[0] (uint64, u8 rec) or acc as double (f32 rec).
+cudaError_t launch_sse(const JobDesc &ref, const uint8_t *rec_u8, int64_t rec_pitch, const float *rec_f32,
+                       int64_t rec_pitch_f32, unsigned long long *acc_u64, double *acc_f64, cudaStream_t s);
+cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double *acc_f64, int use_u64,
+                                double nsamples, double *mse, double *psnr, cudaStream_t s);
+// Fused path for one job: acc is the caller's SSE slot (zeroed by the caller),
+// used as uint64 576*SSE for kind RDCT and as double SSE for kind DCT.
+cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps, cudaStream_t s);
+// Persistent batch kernel over the chunks of one register class
+// (batch_class_of_diag); acc_u64[image] += 576 * SSE.  ctas_per_sm <= 0 uses
+// the occupancy limit.
+int batch_class_of_diag(int d);
+constexpr int kBatchClasses = 3;
+cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
+                               int cls, int ctas_per_sm, int warps, cudaStream_t s);
+// In-place conversion of n uint64 576*SSE slots to double SSE.
+cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
+// Sweep: per-plane zigzag energy, then suffix sums into SSE(r).
+cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
+                         int32_t nplanes, cudaStream_t s);
+cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s);
+
+}  // namespace rdct

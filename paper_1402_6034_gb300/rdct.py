@@ -1,0 +1,336 @@
+"""Thin ctypes binding of librdct (include/rdct.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  torch is used for device memory and streams.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import build_lib
+
+KIND_RDCT = 0
+KIND_DCT = 1
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "invalid shape", 3: "out of memory", 4: "too large",
+           5: "CUDA error", 6: "timeout", 7: "busy", 8: "not found", 9: "cancelled"}
+
+
+class RdctError(RuntimeError):
+    """A librdct call returned a status other than RDCT_OK."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Plane(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("pitch", ctypes.c_int64), ("w", ctypes.c_int32), ("h", ctypes.c_int32)]
+
+
+class Out(ctypes.Structure):
+    _fields_ = [("u8", ctypes.c_void_p), ("f32", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("pitch_f32", ctypes.c_int64)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("src", Plane), ("dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_int64), ("r", ctypes.c_int32),
+                ("image", ctypes.c_int32)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("items_per_chunk", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class HostJob(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("w", ctypes.c_int32), ("h", ctypes.c_int32), ("r", ctypes.c_int32), ("image", ctypes.c_int32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("queue_capacity", ctypes.c_int32), ("streams", ctypes.c_int32), ("max_wait_us", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("pitch", ctypes.c_int64), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("planes", ctypes.c_int32), ("r", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sse", ctypes.c_double), ("mse", ctypes.c_double),
+                ("psnr", ctypes.c_double), ("latency_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("gpixels_per_s", ctypes.c_double),
+                ("peak_resident_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (argtypes) ; all return rdct_status (int) unless listed in _RESTYPE
+_vp, _i32, _i64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "rdct_status_string": [ctypes.c_int],
+    "rdct_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+    "rdct_version": [],
+    "rdct_sync": [_vp],
+    "rdct_forward": [ctypes.POINTER(Plane), _vp, _vp],
+    "rdct_forward_f32": [ctypes.POINTER(Plane), ctypes.c_int, _vp, _vp],
+    "rdct_compress": [_vp, _i64, _i32, _vp, _vp],
+    "rdct_inverse": [_vp, _i64, _i64, _i32, ctypes.c_int, ctypes.POINTER(Out), _vp],
+    "rdct_mse_psnr": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp, _vp],
+    "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
+    "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
+    "rdct_batch_plan_create": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), ctypes.POINTER(_vp)],
+    "rdct_batch_run": [_vp, _vp, _vp],
+    "rdct_batch_run_per_plane": [_vp, _vp, _vp],
+    "rdct_batch_plan_get_tune": [_vp, ctypes.POINTER(Tune)],
+    "rdct_batch_plan_destroy": [_vp],
+    "rdct_autotune": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), _vp],
+    "rdct_pipeline_create": [_i64, _i32, ctypes.POINTER(_vp)],
+    "rdct_pipeline_run": [_vp, ctypes.POINTER(HostJob), _i32, _i32, _vp],
+    "rdct_pipeline_destroy": [_vp],
+    "rdct_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)],
+    "rdct_server_submit": [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
+    "rdct_server_wait": [_vp, ctypes.c_uint64, _i64, ctypes.POINTER(Result)],
+    "rdct_server_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(Result)],
+    "rdct_server_cancel": [_vp, ctypes.c_uint64],
+    "rdct_server_stats_get": [_vp, ctypes.POINTER(ServerStats)],
+    "rdct_server_destroy": [_vp],
+}
+_RESTYPE = {"rdct_status_string": ctypes.c_char_p, "rdct_last_error": ctypes.c_size_t, "rdct_version": ctypes.c_int32}
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librdct.so (building it first if asked); raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"librdct is not built ({path}); run build_lib.build()")
+            build_lib.build()
+        lib = ctypes.CDLL(path)
+        for name, argt in _SIGS.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.argtypes = argt
+            fn.restype = _RESTYPE.get(name, ctypes.c_int)
+        _lib = lib
+        return lib
+
+
+def exported_names() -> list[str]:
+    lib = load()
+    return [n for n in _SIGS if getattr(lib, n, None) is not None]
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        lib = load()
+        buf = ctypes.create_string_buffer(1024)
+        lib.rdct_last_error(buf, 1024)
+        raise RdctError(status, f"{what}: {buf.value.decode(errors='replace')}")
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+
+
+def plane_of(t: torch.Tensor) -> Plane:
+    """A 2-D uint8 CUDA tensor (rows may be padded: stride(1) must be 1) as an rdct_plane."""
+    _require_cuda(t, "plane", torch.uint8)
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("plane must be a 2-D uint8 tensor with unit column stride")
+    return Plane(t.data_ptr(), t.stride(0), t.shape[1], t.shape[0])
+
+
+# ------------------------------------------------------------------- steps
+
+def forward(img: torch.Tensor, stream=None) -> torch.Tensor:
+    """Y = C0 A C0^T per 8x8 block; int32 [h/8, w/8, 8, 8]."""
+    p = plane_of(img)
+    Y = torch.empty((p.h // 8, p.w // 8, 8, 8), dtype=torch.int32, device=img.device)
+    _check(load().rdct_forward(ctypes.byref(p), Y.data_ptr(), _stream(stream)), "rdct_forward")
+    return Y
+
+
+def forward_f32(img: torch.Tensor, kind: int = KIND_RDCT, stream=None) -> torch.Tensor:
+    """Orthonormal coefficients (S Y S or the exact DCT) in FP32; [h/8, w/8, 8, 8]."""
+    p = plane_of(img)
+    Y = torch.empty((p.h // 8, p.w // 8, 8, 8), dtype=torch.float32, device=img.device)
+    _check(load().rdct_forward_f32(ctypes.byref(p), kind, Y.data_ptr(), _stream(stream)), "rdct_forward_f32")
+    return Y
+
+
+def compress(Y: torch.Tensor, r: int, stream=None) -> torch.Tensor:
+    """First r zigzag coefficients of S Y S per block; FP32 [nblocks, r]."""
+    _require_cuda(Y, "Y", torch.int32)
+    Y = Y.contiguous()
+    nb = Y.numel() // 64
+    Yc = torch.empty((nb, r), dtype=torch.float32, device=Y.device)
+    _check(load().rdct_compress(Y.data_ptr(), nb, r, Yc.data_ptr(), _stream(stream)), "rdct_compress")
+    return Yc
+
+
+def inverse(Yc: torch.Tensor, nbw: int, nbh: int, r: int, kind: int = KIND_RDCT, want_u8: bool = True,
+            want_f32: bool = False, stream=None):
+    """Reconstruct from packed coefficients; returns (u8 or None, f32 or None)."""
+    _require_cuda(Yc, "Yc", torch.float32)
+    Yc = Yc.contiguous()
+    dev = Yc.device
+    u8 = torch.empty((nbh * 8, nbw * 8), dtype=torch.uint8, device=dev) if want_u8 else None
+    f32 = torch.empty((nbh * 8, nbw * 8), dtype=torch.float32, device=dev) if want_f32 else None
+    out = Out(u8.data_ptr() if u8 is not None else None, f32.data_ptr() if f32 is not None else None, nbw * 8, nbw * 8)
+    _check(load().rdct_inverse(Yc.data_ptr(), nbw, nbh, r, kind, ctypes.byref(out), _stream(stream)), "rdct_inverse")
+    return u8, f32
+
+
+def mse_psnr(ref: torch.Tensor, rec: torch.Tensor, stream=None):
+    """(MSE, PSNR) of rec (uint8 or float32 plane) against ref, as device float64 scalars."""
+    p = plane_of(ref)
+    _require_cuda(rec, "rec")
+    if rec.dtype == torch.uint8:
+        out = Out(rec.data_ptr(), None, rec.stride(0), 0)
+    elif rec.dtype == torch.float32:
+        out = Out(None, rec.data_ptr(), 0, rec.stride(0))
+    else:
+        raise ValueError("rec must be uint8 or float32")
+    res = torch.empty(2, dtype=torch.float64, device=ref.device)
+    _check(load().rdct_mse_psnr(ctypes.byref(p), ctypes.byref(out), res.data_ptr(), res.data_ptr() + 8,
+                                _stream(stream)), "rdct_mse_psnr")
+    return res[0], res[1]
+
+
+def fused(img: torch.Tensor, r: int, kind: int = KIND_RDCT, want_u8: bool = True, want_f32: bool = False,
+          out_u8: torch.Tensor | None = None, sse: torch.Tensor | None = None, stream=None):
+    """Forward + keep r + inverse + SSE in one kernel; returns (u8 or None, f32 or None, sse [1] float64)."""
+    p = plane_of(img)
+    dev = img.device
+    u8 = out_u8 if out_u8 is not None else (torch.empty((p.h, p.w), dtype=torch.uint8, device=dev) if want_u8 else None)
+    f32 = torch.empty((p.h, p.w), dtype=torch.float32, device=dev) if want_f32 else None
+    if sse is None:
+        sse = torch.empty(1, dtype=torch.float64, device=dev)
+    out = Out(u8.data_ptr() if u8 is not None else None, f32.data_ptr() if f32 is not None else None,
+              u8.stride(0) if u8 is not None else 0, p.w)
+    _check(load().rdct_fused(ctypes.byref(p), r, kind, ctypes.byref(out), sse.data_ptr(), _stream(stream)),
+           "rdct_fused")
+    return u8, f32, sse
+
+
+def sweep(planes, kind: int = KIND_RDCT, stream=None) -> torch.Tensor:
+    """SSE(r) for r = 1..64 per plane; float64 [n, 64].  planes: [n, h, w] uint8 tensor or list of 2-D tensors."""
+    if isinstance(planes, torch.Tensor) and planes.dim() == 3:
+        planes = list(planes.unbind(0))
+    arr = (Plane * len(planes))(*[plane_of(t) for t in planes])
+    dev = planes[0].device
+    out = torch.empty((len(planes), 64), dtype=torch.float64, device=dev)
+    _check(load().rdct_sweep(arr, len(planes), kind, out.data_ptr(), _stream(stream)), "rdct_sweep")
+    return out
+
+
+def psnr_of_mse(mse):
+    """PSNR = 10 log10(255^2 / MSE) for a tensor of MSE values (inf where MSE = 0)."""
+    return 10.0 * torch.log10((255.0 ** 2) / mse)
+
+
+# ----------------------------------------------------------------- batches
+
+@dataclass
+class BatchJob:
+    """One plane of a batch (device tensors)."""
+    src: torch.Tensor
+    dst: torch.Tensor | None
+    r: int
+    image: int
+
+
+class BatchPlan:
+    """A persistent, graph-captured launch over many uneven planes."""
+
+    def __init__(self, jobs: list[BatchJob], nimages: int, tune: dict | None = None):
+        self._keep = [(j.src, j.dst) for j in jobs]
+        self.nimages = nimages
+        arr = (Job * len(jobs))()
+        for i, j in enumerate(jobs):
+            arr[i].src = plane_of(j.src)
+            arr[i].dst = j.dst.data_ptr() if j.dst is not None else None
+            arr[i].dst_pitch = j.dst.stride(0) if j.dst is not None else 0
+            arr[i].r = j.r
+            arr[i].image = j.image
+        self._jobs = arr
+        t = None
+        if tune is not None:
+            t = Tune(tune["warps_per_cta"], tune["ctas_per_sm"], tune["items_per_chunk"],
+                     tune.get("blocks_per_thread", 1))
+        h = ctypes.c_void_p()
+        _check(load().rdct_batch_plan_create(arr, len(jobs), nimages, ctypes.byref(t) if t else None, ctypes.byref(h)),
+               "rdct_batch_plan_create")
+        self._h = h
+
+    @property
+    def tune(self) -> dict:
+        t = Tune()
+        _check(load().rdct_batch_plan_get_tune(self._h, ctypes.byref(t)), "rdct_batch_plan_get_tune")
+        return t.as_dict()
+
+    def run(self, sse: torch.Tensor, stream=None):
+        _check(load().rdct_batch_run(self._h, sse.data_ptr(), _stream(stream)), "rdct_batch_run")
+
+    def run_per_plane(self, sse: torch.Tensor, stream=None):
+        _check(load().rdct_batch_run_per_plane(self._h, sse.data_ptr(), _stream(stream)), "rdct_batch_run_per_plane")
+
+    def close(self):
+        if self._h:
+            load().rdct_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(jobs: list[BatchJob], nimages: int, stream=None) -> dict:
+    arr = (Job * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i].src = plane_of(j.src)
+        arr[i].dst = j.dst.data_ptr() if j.dst is not None else None
+        arr[i].dst_pitch = j.dst.stride(0) if j.dst is not None else 0
+        arr[i].r = j.r
+        arr[i].image = j.image
+    t = Tune()
+    _check(load().rdct_autotune(arr, len(jobs), nimages, ctypes.byref(t), _stream(stream)), "rdct_autotune")
+    return t.as_dict()

@@ -1,0 +1,110 @@
+"""GPU parity of the batched path: uneven planes in one graph launch.
+
+The persistent graph-captured launch must give bit-identical reconstructions
+and SSE to one plain launch per plane, and both must match the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1402_6034_gb300 import rdct, synth
+from tests.gpu_helpers import assert_sse_close, assert_u8_close, cuda_or_skip, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    d = cuda_or_skip()
+    rdct.load()
+    return d
+
+
+def _batch(dev, n_images=12, seed=0, rs=(4, 10, 16, 32), lo=64, hi=264, pitch_pad=0):
+    specs = synth.uneven_specs(n_images, seed=seed, lo=lo, hi=hi, rs=rs)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    pool = synth.crop_pool(pool_side=512, n=2, seed=seed)
+    jobs, host = [], []
+    for i, sp in enumerate(specs):
+        for p in range(sp.planes):
+            img = synth.crop_plane(pool, sp.h, sp.w, rng)
+            pitch = sp.w + pitch_pad
+            buf = torch.zeros(sp.h * pitch + 32, dtype=torch.uint8, device=dev)
+            src = torch.as_strided(buf, (sp.h, sp.w), (pitch, 1))
+            src.copy_(to_dev(img, dev))
+            dst = torch.zeros((sp.h, sp.w), dtype=torch.uint8, device=dev)
+            jobs.append(rdct.BatchJob(src, dst, sp.r, i))
+            host.append((img, sp.r, i))
+    return specs, jobs, host
+
+
+def _check_against_oracle(specs, jobs, host, sse):
+    per_image = np.zeros(len(specs))
+    npix = np.zeros(len(specs))
+    for j, (img, r, i) in zip(jobs, host):
+        xo, uo, so, _ = orc.fused(img, r)
+        assert_u8_close(j.dst.cpu().numpy(), uo, xo, tie_window=1e-6)
+        per_image[i] += so
+        npix[i] += img.size
+    for i in range(len(specs)):
+        assert_sse_close(sse[i], per_image[i], int(npix[i]))
+        assert sse[i] == pytest.approx(per_image[i], rel=1e-9, abs=1e-9)
+
+
+@pytest.mark.parametrize("pitch_pad", [0, 8, 3])
+def test_batch_graph_matches_oracle(dev, pitch_pad):
+    specs, jobs, host = _batch(dev, pitch_pad=pitch_pad)
+    plan = rdct.BatchPlan(jobs, len(specs))
+    sse = torch.empty(len(specs), dtype=torch.float64, device=dev)
+    plan.run(sse)
+    plan.run(sse)  # graph replay
+    torch.cuda.synchronize()
+    _check_against_oracle(specs, jobs, host, sse.cpu().numpy())
+    plan.close()
+
+
+def test_batch_every_r_class(dev):
+    """Plans that mix all three register classes (r up to 64)."""
+    specs, jobs, host = _batch(dev, n_images=16, seed=5, rs=(1, 3, 6, 10, 15, 21, 28, 36, 45, 55, 64))
+    plan = rdct.BatchPlan(jobs, len(specs))
+    sse = torch.empty(len(specs), dtype=torch.float64, device=dev)
+    plan.run(sse)
+    torch.cuda.synchronize()
+    _check_against_oracle(specs, jobs, host, sse.cpu().numpy())
+
+
+def test_batch_equals_per_plane(dev):
+    specs, jobs, host = _batch(dev, n_images=20, seed=9)
+    plan = rdct.BatchPlan(jobs, len(specs), tune={"warps_per_cta": 4, "ctas_per_sm": 2, "items_per_chunk": 3})
+    sse_b = torch.empty(len(specs), dtype=torch.float64, device=dev)
+    plan.run(sse_b)
+    outs_b = [j.dst.clone() for j in jobs]
+    for j in jobs:
+        j.dst.zero_()
+    sse_p = torch.empty(len(specs), dtype=torch.float64, device=dev)
+    plan.run_per_plane(sse_p)
+    torch.cuda.synchronize()
+    assert torch.equal(sse_b, sse_p)
+    for a, j in zip(outs_b, jobs):
+        assert torch.equal(a, j.dst)
+
+
+def test_autotune_picks_a_valid_shape(dev):
+    specs, jobs, host = _batch(dev, n_images=8, seed=11)
+    t = rdct.autotune(jobs, len(specs))
+    assert 1 <= t["warps_per_cta"] <= 32 and t["items_per_chunk"] >= 1
+    plan = rdct.BatchPlan(jobs, len(specs))  # picks the cached tune
+    assert plan.tune == t
+    sse = torch.empty(len(specs), dtype=torch.float64, device=dev)
+    plan.run(sse)
+    torch.cuda.synchronize()
+    _check_against_oracle(specs, jobs, host, sse.cpu().numpy())
+
+
+def test_batch_rejects_bad_jobs(dev):
+    src = torch.zeros((8, 8), dtype=torch.uint8, device=dev)
+    with pytest.raises(rdct.RdctError):
+        rdct.BatchPlan([rdct.BatchJob(src, None, 0, 0)], 1)
+    with pytest.raises(rdct.RdctError):
+        rdct.BatchPlan([rdct.BatchJob(src, None, 10, 3)], 1)
