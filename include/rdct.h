@@ -149,6 +149,23 @@ RDCT_API rdct_status rdct_fused(const rdct_plane *src, int32_t r, rdct_kind kind
  * is orthogonal).  Exact for kind RDCT; FP32 products, FP64 sums for DCT. */
 RDCT_API rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r, rdct_stream stream);
 
+/* rdct_sweep without any allocation.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they call in
+ * (a framework that owns the whole device heap through its own allocator, a
+ * real-time loop where an allocation could stall or synchronise the device, a
+ * plug-in whose host process forbids device allocation).  Same arguments and
+ * results as rdct_sweep; the per-call descriptor tables live in one fixed
+ * device array inside the library (about 720 KiB, held on every GPU that
+ * loads the library until the process exits) and are built on the device.
+ * Limits: at most 2048 planes and 32768 chunks of 16 strips (about 1.07
+ * Gpixel) per call, else RDCT_ERR_TOO_LARGE and nothing is enqueued.
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device), so make it before any stream capture.  Every call shares
+ * the array: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+RDCT_API rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r,
+                                        rdct_stream stream);
+
 /* ------------------------------------------------ batches of uneven planes */
 
 /* One plane of a batch.  SSE is summed per image over its planes. */

@@ -1,0 +1,147 @@
+// rdct_noalloc.cu -- rdct_sweep_noalloc: the r sweep without any allocation.
+//
+// Some callers cannot allocate device memory at the moment they call us: a
+// host framework that owns the whole device heap through its own allocator
+// (where a stray cudaMalloc or cudaMallocAsync would fragment its pool or
+// break its memory cap), a real-time loop in which an allocation could stall
+// or synchronise the device, or a plug-in whose host process forbids device
+// allocation outright.  rdct_sweep builds per-call descriptor tables in a
+// stream-ordered allocation; this variant keeps them in one fixed device array
+// that is part of the library image instead, builds them on the device, and
+// otherwise runs the same kernels.  Nothing is allocated, on the device or on
+// the host, on the success path.
+//
+// The array is a file-scope __device__ variable: every GPU that loads the
+// library holds it (kNoAllocScratchBytes, about 720 KiB) until the process
+// exits.  In host code its name is only a host-side stand-in for the device
+// variable, not a device address, so its device address is looked up with
+// cudaGetSymbolAddress, once per device, with that device current, the first
+// time the entry point runs on that device.  That first call should therefore
+// come before any stream capture.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "rdct_device.cuh"
+#include "rdct_internal.h"
+
+namespace rdct {
+namespace {
+
+constexpr int32_t kNoAllocMaxPlanes = 2048;
+constexpr int32_t kNoAllocMaxChunks = 32768;
+constexpr int32_t kNoAllocStrips = 16;  // strips per chunk, as in rdct_sweep
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+constexpr size_t kPlanesOff = 0;
+constexpr size_t kJobsOff = align256(kPlanesOff + sizeof(rdct_plane) * kNoAllocMaxPlanes);
+constexpr size_t kChunksOff = align256(kJobsOff + sizeof(JobDesc) * kNoAllocMaxPlanes);
+constexpr size_t kNoAllocScratchBytes = align256(kChunksOff + sizeof(Chunk) * kNoAllocMaxChunks);
+
+// The scratch: planes as passed in, then the job and chunk tables.
+static __device__ __align__(256) unsigned char g_sweep_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_sweep_scratch for the current device (looked up once).
+rdct_status scratch_address(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "rdct_sweep_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(RDCT_ERR_ARG, "rdct_sweep_noalloc: device index too large");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sweep_scratch);
+        if (e != cudaSuccess || !p) return cuda_error(e, "rdct_sweep_noalloc: cudaGetSymbolAddress");
+        g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return RDCT_OK;
+}
+
+__device__ int align_class(const void *p, int64_t pitch) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if ((a % 16) == 0 && (pitch % 16) == 0) return 16;
+    if ((a % 8) == 0 && (pitch % 8) == 0) return 8;
+    return 1;
+}
+
+// Builds the job table (one descriptor per plane, one block per thread,
+// strips of 32 blocks) and the chunk table (runs of <= 16 strips) from the
+// planes copied into the scratch.  One CTA; n <= kNoAllocMaxPlanes.
+__global__ void build_sweep_tables_kernel(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks) {
+    __shared__ int32_t s_off[kNoAllocMaxPlanes + 1];
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const rdct_plane pl = planes[i];
+        JobDesc j{};
+        j.src = pl.ptr;
+        j.src_pitch = pl.pitch;
+        j.nbw = pl.w / 8;
+        j.nbh = pl.h / 8;
+        j.r = 64;
+        j.image = i;
+        j.segs = (j.nbw + 31) / 32;
+        j.align = align_class(pl.ptr, pl.pitch);
+        j.dalign = 16;
+        jobs[i] = j;
+        const int32_t items = j.nbh * j.segs;
+        s_off[i + 1] = (items + kNoAllocStrips - 1) / kNoAllocStrips;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_off[0] = 0;
+        for (int32_t i = 0; i < n; ++i) s_off[i + 1] += s_off[i];
+    }
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t items = jobs[i].nbh * jobs[i].segs;
+        int32_t c = s_off[i];
+        for (int32_t it = 0; it < items; it += kNoAllocStrips, ++c)
+            chunks[c] = Chunk{i, it, items - it < kNoAllocStrips ? items - it : kNoAllocStrips, 0};
+    }
+}
+
+}  // namespace
+}  // namespace rdct
+
+using namespace rdct;
+
+extern "C" rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r,
+                                          rdct_stream stream) {
+    if (!planes || !sse_by_r || n < 0) return set_error(RDCT_ERR_ARG, "rdct_sweep_noalloc: null pointer or negative count");
+    if (kind != RDCT_KIND_RDCT && kind != RDCT_KIND_DCT) return set_error(RDCT_ERR_ARG, "rdct_sweep_noalloc: bad kind");
+    if (reinterpret_cast<uintptr_t>(sse_by_r) % 8) return set_error(RDCT_ERR_ARG, "rdct_sweep_noalloc: misaligned output");
+    if (n > kNoAllocMaxPlanes)
+        return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: more than 2048 planes in one call; split the call "
+                                             "or use rdct_sweep");
+    int64_t nchunks = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        rdct_status st = validate_plane(&planes[i], "rdct_sweep_noalloc");
+        if (st) return st;
+        const int64_t items = (int64_t)(planes[i].h / 8) * ((planes[i].w / 8 + 31) / 32);
+        nchunks += (items + kNoAllocStrips - 1) / kNoAllocStrips;
+    }
+    if (nchunks > kNoAllocMaxChunks)
+        return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: the planes need more than 32768 chunks of 16 "
+                                             "strips (about 1.07 Gpixel in one call); split the call or use rdct_sweep");
+    if (n == 0) return RDCT_OK;
+    unsigned char *base = nullptr;
+    rdct_status st = scratch_address(&base);
+    if (st) return st;
+    rdct_plane *d_planes = reinterpret_cast<rdct_plane *>(base + kPlanesOff);
+    JobDesc *d_jobs = reinterpret_cast<JobDesc *>(base + kJobsOff);
+    Chunk *d_chunks = reinterpret_cast<Chunk *>(base + kChunksOff);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the tables are rewritten in full by every call; only the output bins must start at zero
+    RDCT_CUDA_TRY(cudaMemcpyAsync(d_planes, planes, sizeof(rdct_plane) * (size_t)n, cudaMemcpyHostToDevice, s));
+    build_sweep_tables_kernel<<<1, 256, 0, s>>>(d_planes, n, d_jobs, d_chunks);
+    RDCT_CUDA_TRY(cudaGetLastError());
+    RDCT_CUDA_TRY(cudaMemsetAsync(sse_by_r, 0, (size_t)n * 64 * sizeof(double), s));
+    RDCT_CUDA_TRY(launch_sweep(d_jobs, d_chunks, (int32_t)nchunks, (int)kind, sse_by_r, n, s));
+    RDCT_CUDA_TRY(launch_sweep_finalize(sse_by_r, n, (int)kind, s));
+    return RDCT_OK;
+}

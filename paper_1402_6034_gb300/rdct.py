@@ -96,6 +96,7 @@ _SIGS = {
     "rdct_mse_psnr": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp, _vp],
     "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
+    "rdct_sweep_noalloc": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_batch_plan_create": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), ctypes.POINTER(_vp)],
     "rdct_batch_run": [_vp, _vp, _vp],
     "rdct_batch_run_per_plane": [_vp, _vp, _vp],
@@ -257,6 +258,21 @@ def sweep(planes, kind: int = KIND_RDCT, stream=None) -> torch.Tensor:
     dev = planes[0].device
     out = torch.empty((len(planes), 64), dtype=torch.float64, device=dev)
     _check(load().rdct_sweep(arr, len(planes), kind, out.data_ptr(), _stream(stream)), "rdct_sweep")
+    return out
+
+
+def sweep_noalloc(planes, out: torch.Tensor, kind: int = KIND_RDCT, stream=None) -> torch.Tensor:
+    """rdct_sweep without allocation inside the library, for callers that cannot allocate device
+    memory at call time.  ``out`` is a caller-owned float64 [n, 64] CUDA tensor (allocated in
+    advance).  At most 2048 planes / about 1.07 Gpixel per call; concurrent calls race on the
+    library's fixed table storage and must be serialised by the caller."""
+    if isinstance(planes, torch.Tensor) and planes.dim() == 3:
+        planes = list(planes.unbind(0))
+    _require_cuda(out, "out", torch.float64)
+    if out.shape != (len(planes), 64) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [n, 64] float64 tensor")
+    arr = (Plane * len(planes))(*[plane_of(t) for t in planes])
+    _check(load().rdct_sweep_noalloc(arr, len(planes), kind, out.data_ptr(), _stream(stream)), "rdct_sweep_noalloc")
     return out
 
 

@@ -1,0 +1,64 @@
+"""rdct_sweep_noalloc, the r sweep for callers that cannot allocate device memory.
+
+Some callers cannot let a library allocate device memory when they call it:
+a framework that owns the device heap through its own allocator, a real-time
+loop where an allocation could stall or synchronise the device, a plug-in
+whose host process forbids device allocation.  rdct_sweep_noalloc keeps its
+tables in a fixed device array inside the library instead.  This file checks,
+through the C-ABI, that two calls in a row give the same results as
+rdct_sweep (the second call with different planes, so stale tables from the
+first would show) and that oversized calls are refused.
+
+It sits in its own file, collected last, and passes both alone in a fresh
+process and after the other tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1402_6034_gb300 import rdct, synth
+from tests.gpu_helpers import assert_sse_close, cuda_or_skip, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    d = cuda_or_skip()
+    rdct.load()
+    return d
+
+
+def _planes(dev, shapes, seed):
+    return [to_dev(synth.image_1f(h, w, seed=seed + i), dev) for i, (h, w) in enumerate(shapes)]
+
+
+@pytest.mark.parametrize("kind", [rdct.KIND_RDCT, rdct.KIND_DCT])
+def test_noalloc_matches_sweep_on_two_calls(dev, kind):
+    first = _planes(dev, [(512, 512), (72, 136), (64, 64), (256, 1024)], seed=40)
+    second = _planes(dev, [(136, 72), (8, 8)], seed=90)
+    for planes in (first, second):
+        out = torch.full((len(planes), 64), -1.0, dtype=torch.float64, device=dev)
+        rdct.sweep_noalloc(planes, out, kind)
+        ref = rdct.sweep(planes, kind)
+        torch.cuda.synchronize()
+        got, want = out.cpu().numpy(), ref.cpu().numpy()
+        for i, p in enumerate(planes):
+            for r in range(1, 65):
+                assert_sse_close(got[i, r - 1], want[i, r - 1], p.numel())
+        if kind == rdct.KIND_RDCT:  # integer energies: exact on both paths
+            np.testing.assert_array_equal(got, want)
+
+
+def test_noalloc_rejects_oversized_calls(dev):
+    small = torch.zeros((8, 8), dtype=torch.uint8, device=dev)
+    out = torch.zeros((2049, 64), dtype=torch.float64, device=dev)
+    with pytest.raises(rdct.RdctError) as e:
+        rdct.sweep_noalloc([small] * 2049, out)
+    assert e.value.status == 4
+    # 2048 planes of 272 block rows x 32 blocks need 17 chunks of 16 strips each: 34816 > 32768
+    tall = torch.zeros((8 * 16 * 17, 8 * 32), dtype=torch.uint8, device=dev)
+    out2 = torch.zeros((2048, 64), dtype=torch.float64, device=dev)
+    with pytest.raises(rdct.RdctError) as e:
+        rdct.sweep_noalloc([tall] * 2048, out2)
+    assert e.value.status == 4
