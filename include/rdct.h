@@ -182,7 +182,8 @@ typedef struct {
     int32_t warps_per_cta;   /* 1..8 */
     int32_t ctas_per_sm;     /* grid = ctas_per_sm * SM count */
     int32_t items_per_chunk; /* strips handed to a warp at a time */
-    int32_t blocks_per_thread; /* 1 or 2 horizontally adjacent 8x8 blocks per thread */
+    int32_t blocks_per_thread; /* 2: dp4a/f32x2 kernel, two vertically adjacent 8x8 blocks per
+                                  thread, 4 warps per CTA; 1: scalar kernel, one block per thread */
 } rdct_tune;
 
 typedef struct rdct_plan rdct_plan;
@@ -283,6 +284,27 @@ RDCT_API rdct_status rdct_server_cancel(rdct_server *server, uint64_t ticket);
 RDCT_API rdct_status rdct_server_stats_get(rdct_server *server, rdct_server_stats *stats);
 /* Drains outstanding work, then frees everything. */
 RDCT_API rdct_status rdct_server_destroy(rdct_server *server);
+
+/* Test hook for failure handling without a GPU fault: the next n buffer
+ * admissions fail as if the device budget were exhausted; the affected
+ * requests stay queued and are admitted once the failures are used up. */
+RDCT_API rdct_status rdct_server_inject_alloc_failures(rdct_server *server, int32_t n);
+
+/* ------------------------------------------- device-budget arena (host side) */
+
+/* The first-fit sub-allocator the server uses to place request buffers in its
+ * fixed device budget.  It manages offsets in [0, size) only (no memory of
+ * its own), aligns every block to `align` bytes (a power of two) and merges
+ * neighbouring free blocks on free. */
+typedef struct rdct_arena rdct_arena;
+RDCT_API rdct_status rdct_arena_create(int64_t size, int64_t align, rdct_arena **arena);
+/* RDCT_ERR_OOM when no free block is large enough (nothing changes). */
+RDCT_API rdct_status rdct_arena_alloc(rdct_arena *arena, int64_t bytes, int64_t *offset);
+/* RDCT_ERR_NOT_FOUND when offset is not the start of a live block. */
+RDCT_API rdct_status rdct_arena_free(rdct_arena *arena, int64_t offset);
+RDCT_API int64_t rdct_arena_used(const rdct_arena *arena);
+RDCT_API int64_t rdct_arena_largest_free(const rdct_arena *arena);
+RDCT_API rdct_status rdct_arena_destroy(rdct_arena *arena);
 
 #ifdef __cplusplus
 }

@@ -29,12 +29,14 @@ struct rdct_plan {
     std::vector<JobDesc> jobs;     // host copy, segs computed for the plan's tile
     std::vector<JobDesc> jobs_pp;  // per-plane launches (one block per thread)
     std::vector<Chunk> chunks;
-    int32_t class_begin[kBatchClasses + 1] = {0};
+    int32_t group_begin[kBatchGroups + 1] = {0};  // chunk ranges per launch group
     JobDesc *d_jobs = nullptr;
     Chunk *d_chunks = nullptr;
     // graph cache: one executable per (sse pointer)
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t branch[kBatchGroups] = {nullptr};  // capture-time forks: groups run as parallel graph branches
+    cudaEvent_t fork = nullptr, join[kBatchGroups] = {nullptr};
     cudaGraphExec_t exec = nullptr;
     double *exec_sse = nullptr;
 };
@@ -43,18 +45,18 @@ namespace {
 
 rdct_tune default_tune() {
     rdct_tune t{};
-    t.warps_per_cta = 8;
+    t.warps_per_cta = 4;
     t.ctas_per_sm = 0;  // occupancy limit
     t.items_per_chunk = 8;
-    t.blocks_per_thread = 1;
+    t.blocks_per_thread = 2;
     return t;
 }
 
 rdct_status validate_tune(const rdct_tune &t) {
     if (t.warps_per_cta < 1 || t.warps_per_cta > 8 || t.ctas_per_sm < 0 || t.ctas_per_sm > 64 ||
-        t.items_per_chunk < 1 || t.items_per_chunk > 4096 || t.blocks_per_thread != 1)
+        t.items_per_chunk < 1 || t.items_per_chunk > 4096 || (t.blocks_per_thread != 1 && t.blocks_per_thread != 2))
         return set_error(RDCT_ERR_ARG, "rdct_tune: out of range (warps 1..8, ctas_per_sm 0..64, "
-                                       "items_per_chunk 1..4096, blocks_per_thread 1)");
+                                       "items_per_chunk 1..4096, blocks_per_thread 1 or 2)");
     return RDCT_OK;
 }
 
@@ -75,40 +77,49 @@ rdct_status validate_jobs(const rdct_job *jobs, int32_t njobs, int32_t nimages) 
 }
 
 void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
-    const int bpt = p->tune.blocks_per_thread;
+    const int vrows = p->tune.blocks_per_thread == 2 ? kFusedVRows : 1;
     p->jobs.resize(njobs);
     p->jobs_pp.resize(njobs);
     for (int32_t i = 0; i < njobs; ++i) {
         const rdct_job &j = jobs[i];
-        p->jobs[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, bpt);
-        p->jobs_pp[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, 1);
+        p->jobs[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, 1);
+        p->jobs_pp[i] = p->jobs[i];
     }
     std::vector<Chunk> ch;
     const int per = p->tune.items_per_chunk;
     for (int32_t i = 0; i < njobs; ++i) {
-        const int items = p->jobs[i].nbh * p->jobs[i].segs;
+        const int items = strips_of(p->jobs[i], vrows);
         const int d = diag_class_host(p->jobs[i].r);
         for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), d});
     }
-    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) {
-        const int ca = batch_class_of_diag(a.diag), cb = batch_class_of_diag(b.diag);
-        if (ca != cb) return ca < cb;
-        return a.diag < b.diag;
-    });
+    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) { return a.diag < b.diag; });
     p->chunks = std::move(ch);
-    for (int c = 0; c <= kBatchClasses; ++c) p->class_begin[c] = 0;
-    for (const Chunk &c : p->chunks) p->class_begin[batch_class_of_diag(c.diag) + 1]++;
-    for (int c = 0; c < kBatchClasses; ++c) p->class_begin[c + 1] += p->class_begin[c];
+    const int bpt = p->tune.blocks_per_thread;
+    for (int g = 0; g <= kBatchGroups; ++g) p->group_begin[g] = 0;
+    for (const Chunk &c : p->chunks) p->group_begin[batch_group_of_diag(c.diag, bpt) + 1]++;
+    for (int g = 0; g < kBatchGroups; ++g) p->group_begin[g + 1] += p->group_begin[g];
 }
 
+// memset -> one persistent kernel per non-empty group (forked onto their own
+// streams when there are several, so they become parallel graph branches and
+// fill the GPU together) -> join -> in-place 576*SSE to SSE.
 cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
-    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c) {
-        const int32_t b = p->class_begin[c], n = p->class_begin[c + 1] - b;
-        if (n > 0)
-            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, c, p->tune.ctas_per_sm, p->tune.warps_per_cta,
-                                   s);
+    int groups = 0;
+    for (int g = 0; g < kBatchGroups; ++g) groups += p->group_begin[g + 1] > p->group_begin[g];
+    const bool fork = groups > 1;
+    if (fork && e == cudaSuccess) e = cudaEventRecord(p->fork, s);
+    for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
+        const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
+        if (n == 0) continue;
+        cudaStream_t gs = fork ? p->branch[g] : s;
+        if (fork) e = cudaStreamWaitEvent(gs, p->fork, 0);
+        if (e == cudaSuccess)
+            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm, p->tune.warps_per_cta,
+                                   p->tune.blocks_per_thread, gs);
+        if (fork && e == cudaSuccess) e = cudaEventRecord(p->join[g], gs);
+        if (fork && e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join[g], 0);
     }
     if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
     return e;
@@ -120,11 +131,12 @@ std::map<std::string, rdct_tune> g_tune_cache;
 std::string shape_key(const rdct_job *jobs, int32_t njobs) {
     // shape class: job count, total blocks (log2 bucket) and blocks per r class
     int64_t blocks = 0;
-    int64_t per_class[kBatchClasses] = {0};
+    int64_t per_class[3] = {0};
     for (int32_t i = 0; i < njobs; ++i) {
         const int64_t b = (int64_t)(jobs[i].src.w / 8) * (jobs[i].src.h / 8);
         blocks += b;
-        per_class[batch_class_of_diag(diag_class_host(jobs[i].r))] += b;
+        const int d = diag_class_host(jobs[i].r);
+        per_class[d <= 5 ? 0 : (d <= 8 ? 1 : 2)] += b;
     }
     int dev = 0;
     cudaGetDevice(&dev);
@@ -132,7 +144,7 @@ std::string shape_key(const rdct_job *jobs, int32_t njobs) {
     int lg = 0;
     while ((int64_t)1 << (lg + 1) <= blocks) ++lg;
     k += ":b" + std::to_string(lg);
-    for (int c = 0; c < kBatchClasses; ++c) k += ":" + std::to_string(blocks ? (int)(10 * per_class[c] / blocks) : 0);
+    for (int c = 0; c < 3; ++c) k += ":" + std::to_string(blocks ? (int)(10 * per_class[c] / blocks) : 0);
     return k;
 }
 
@@ -173,6 +185,12 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     if (jb) e = cudaMemcpy(p->d_jobs, p->jobs.data(), jb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && cb) e = cudaMemcpy(p->d_chunks, p->chunks.data(), cb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
+        if (p->group_begin[g + 1] == p->group_begin[g]) continue;
+        e = cudaStreamCreateWithFlags(&p->branch[g], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[g], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         rdct_batch_plan_destroy(p);
         return cuda_error(e, "rdct_batch_plan_create");
@@ -234,6 +252,11 @@ rdct_status rdct_batch_plan_destroy(rdct_plan *p) {
         cudaStreamSynchronize(p->cap_stream);
         cudaStreamDestroy(p->cap_stream);
     }
+    for (int g = 0; g < kBatchGroups; ++g) {
+        if (p->branch[g]) cudaStreamDestroy(p->branch[g]);
+        if (p->join[g]) cudaEventDestroy(p->join[g]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_chunks) cudaFree(p->d_chunks);
     delete p;
@@ -252,14 +275,15 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     std::vector<rdct_tune> cands;
-    for (int warps : {2, 4, 8})
-        for (int ctas : {0, 1, 2})
+    // blocks_per_thread 2: the dp4a/f32x2 kernel (fixed 4 warps); 1: the scalar kernel
+    for (int bpt : {2, 1})
+        for (int ctas : {0, 2, 4})
             for (int items : {2, 4, 8, 16, 32}) {
                 rdct_tune t{};
-                t.warps_per_cta = warps;
+                t.warps_per_cta = bpt == 2 ? 4 : 8;
                 t.ctas_per_sm = ctas;
                 t.items_per_chunk = items;
-                t.blocks_per_thread = 1;
+                t.blocks_per_thread = bpt;
                 cands.push_back(t);
             }
     float best_ms = 1e30f;

@@ -215,10 +215,11 @@ __device__ __forceinline__ unsigned long long fused_block_rdct(const uint32_t w[
         c0t_inverse<rm>(U[n], E);
         if constexpr (OUT & 1) {
             if (dst != nullptr) {  // uniform: batch planes may have no uint8 output
-                uint32_t q[8];
+                int q[8];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) q[m] = round_u8_from_576(E[m]);
-                store_row_u8(dst + n * dpitch, dalign, pack4(q[0], q[1], q[2], q[3]), pack4(q[4], q[5], q[6], q[7]));
+                for (int m = 0; m < 8; ++m) q[m] = q_from_576(E[m]);
+                store_row_u8(dst + n * dpitch, dalign, pack4_sat(q[0], q[1], q[2], q[3]),
+                             pack4_sat(q[4], q[5], q[6], q[7]));
             }
         }
         if constexpr (OUT & 2) {
@@ -276,10 +277,11 @@ __device__ __forceinline__ float fused_block_dct(const uint32_t w[16], int r, co
             sse = __fmaf_rn(e, e, sse);
         }
         if constexpr (OUT & 1) {
-            uint32_t q[8];
+            int q[8];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) q[m] = round_u8(X[m]);
-            store_row_u8(dst + n * dpitch, dalign, pack4(q[0], q[1], q[2], q[3]), pack4(q[4], q[5], q[6], q[7]));
+            for (int m = 0; m < 8; ++m) q[m] = q_of(X[m]);
+            store_row_u8(dst + n * dpitch, dalign, pack4_sat(q[0], q[1], q[2], q[3]),
+                         pack4_sat(q[4], q[5], q[6], q[7]));
         }
         if constexpr (OUT & 2) store_row_f32(dstf + n * fpitch, X);
     }

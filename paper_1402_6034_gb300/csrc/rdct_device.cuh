@@ -67,7 +67,7 @@ __device__ __forceinline__ void static_for(F &&f) {
 // X = C0 x for one 8-vector (22 additions).  V is any type with + and -
 // (int32 here; exact since |X| <= 8 * max|x|).
 template <typename V>
-__device__ __forceinline__ void c0_forward(const V x[8], V X[8]) {
+__host__ __device__ constexpr void c0_forward(const V x[8], V X[8]) {
     const V a0 = x[0] + x[7], a1 = x[1] + x[6], a2 = x[2] + x[5], a3 = x[3] + x[4];
     const V b0 = x[0] - x[7], b1 = x[1] - x[6], b2 = x[2] - x[5], b3 = x[3] - x[4];
     const V s03 = a0 + a3, s12 = a1 + a2;
@@ -81,50 +81,70 @@ __device__ __forceinline__ void c0_forward(const V x[8], V X[8]) {
     X[7] = b2 - b1 - b3;  // row 7: 0 -1  1 -1  1 -1  1  0
 }
 
+// C0[k][n], read off the butterfly itself (its response to the unit vector e_n).
+__host__ __device__ constexpr int c0_entry(int k, int n) {
+    int x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int X[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    x[n] = 1;
+    c0_forward(x, X);
+    return X[k];
+}
+// Row k of C0 as four signed bytes per word: half 0 = columns 0..3, half 1 = 4..7
+// (operands of a byte dot product with four packed pixels).
+__host__ __device__ constexpr unsigned c0_row_word(int k, int half) {
+    unsigned w = 0;
+    for (int b = 0; b < 4; ++b) w |= ((unsigned)c0_entry(k, 4 * half + b) & 0xFFu) << (8 * b);
+    return w;
+}
+
 // ---------------------------------------------- C0^T inverse butterfly (FP32)
 //
 // x = C0^T X for one 8-vector, in FP32, skipping inputs known at compile time
 // to be zero (bit k of M set = X[k] may be non-zero).  All values on the RDCT
 // path are integers below 2^24 in magnitude, so FP32 is exact here.
 
-template <bool A, bool B>
-__device__ __forceinline__ float padd(float a, float b) {
+template <bool A, bool B, typename V>
+__device__ __forceinline__ V padd(V a, V b) {
     if constexpr (A && B) return a + b;
     else if constexpr (A) return a;
     else if constexpr (B) return b;
-    else return 0.0f;
+    else return V{};
 }
-template <bool A, bool B>
-__device__ __forceinline__ float psub(float a, float b) {
+template <bool A, bool B, typename V>
+__device__ __forceinline__ V psub(V a, V b) {
     if constexpr (A && B) return a - b;
     else if constexpr (A) return a;
     else if constexpr (B) return -b;
-    else return 0.0f;
+    else return V{};
 }
 
-template <unsigned M>
-__device__ __forceinline__ void c0t_inverse(const float X[8], float x[8]) {
+// x = C0^T X for one 8-vector (22 additions at most), skipping inputs known
+// at compile time to be zero (bit k of M set = X[k] may be non-zero).  V is
+// float or a packed pair of floats; on the RDCT path every value is an
+// integer (in some fixed unit) below 2^24 in magnitude, so it is exact.
+template <unsigned M, typename V>
+__device__ __forceinline__ void c0t_inverse(const V X[8], V x[8]) {
     constexpr bool p0 = M & 1u, p1 = (M >> 1) & 1u, p2 = (M >> 2) & 1u, p3 = (M >> 3) & 1u;
     constexpr bool p4 = (M >> 4) & 1u, p5 = (M >> 5) & 1u, p6 = (M >> 6) & 1u, p7 = (M >> 7) & 1u;
     // even half: columns n = 0..3 of rows 0, 2, 4, 6
     constexpr bool pp = p0 || p4;
-    const float p = padd<p0, p4>(X[0], X[4]);
-    const float q = psub<p0, p4>(X[0], X[4]);
+    const V p = padd<p0, p4>(X[0], X[4]);
+    const V q = psub<p0, p4>(X[0], X[4]);
     constexpr bool e0 = pp || p2, e1 = pp || p6;
-    const float ea0 = padd<pp, p2>(p, X[2]);  // x0 + x7 part
-    const float ea3 = psub<pp, p2>(p, X[2]);
-    const float ea1 = psub<pp, p6>(q, X[6]);
-    const float ea2 = padd<pp, p6>(q, X[6]);
+    const V ea0 = padd<pp, p2>(p, X[2]);
+    const V ea3 = psub<pp, p2>(p, X[2]);
+    const V ea1 = psub<pp, p6>(q, X[6]);
+    const V ea2 = padd<pp, p6>(q, X[6]);
     // odd half: columns n = 0..3 of rows 1, 3, 5, 7
     constexpr bool p13 = p1 || p3, p15 = p1 || p5, p35 = p3 || p5;
-    const float t13 = padd<p1, p3>(X[1], X[3]);
-    const float ob0 = padd<p13, p5>(t13, X[5]);                 // X1 + X3 + X5
-    const float t15 = psub<p1, p5>(X[1], X[5]);
-    const float ob1 = psub<p15, p7>(t15, X[7]);                 // X1 - X5 - X7
-    const float t13m = psub<p1, p3>(X[1], X[3]);
-    const float ob2 = padd<p13, p7>(t13m, X[7]);                // X1 - X3 + X7
-    const float t53 = psub<p5, p3>(X[5], X[3]);
-    const float ob3 = psub<p35, p7>(t53, X[7]);                 // -X3 + X5 - X7
+    const V t13 = padd<p1, p3>(X[1], X[3]);
+    const V ob0 = padd<p13, p5>(t13, X[5]);   // X1 + X3 + X5
+    const V t15 = psub<p1, p5>(X[1], X[5]);
+    const V ob1 = psub<p15, p7>(t15, X[7]);   // X1 - X5 - X7
+    const V t13m = psub<p1, p3>(X[1], X[3]);
+    const V ob2 = padd<p13, p7>(t13m, X[7]);  // X1 - X3 + X7
+    const V t53 = psub<p5, p3>(X[5], X[3]);
+    const V ob3 = psub<p35, p7>(t53, X[7]);   // -X3 + X5 - X7
     constexpr bool o0 = p13 || p5, o1 = p15 || p7, o2 = p13 || p7, o3 = p35 || p7;
     constexpr bool e2 = e1, e3 = e0;
     x[0] = padd<e0, o0>(ea0, ob0);
@@ -167,23 +187,27 @@ __device__ __forceinline__ uint32_t byte_of(uint32_t w, int k) {
     return __byte_perm(w, 0u, 0x4440u + (unsigned)k);  // zero-extended byte k
 }
 
-// Round an exact integer multiple of 1/576 (given as e = 576 x) to the nearest
-// integer and clamp to [0, 255]; returns the byte in bits 0..7 of the result.
-// sat(e / (576*255)) * 255 + 1.5*2^23 leaves round-to-nearest(x) in the low
-// mantissa bits; non-half values are at least 1/576 away from a rounding
-// boundary, far more than the FP32 error of the two steps.
-__device__ __forceinline__ uint32_t round_u8_from_576(float e) {
-    const float t = __saturatef(e * (1.0f / (576.0f * 255.0f)));
-    return __float_as_uint(__fmaf_rn(t, 255.0f, 12582912.0f));
+// Rounding to 8 bits without conversion instructions.  A float times 2^-149
+// lands in the subnormal range, where the representable values are the
+// integer multiples of 2^-149: the multiplication rounds its exact product to
+// the nearest integer (ties to even) and leaves that integer in the bit
+// pattern; negative values carry the sign bit, so as int32 they are negative.
+// cvt.pack.sat then clamps to [0, 255] while packing.
+//
+// q_from_576(e), e = 576 x an exact integer: e * 2^-149 is exact, and the
+// multiplication by fl(1/576) (slightly above 1/576) rounds x to the nearest
+// integer, exact halves upward.
+__device__ __forceinline__ int q_from_576(float e) {
+    return __float_as_int(__fmul_rn(__fmul_rn(e, 0x1p-149f), 1.0f / 576.0f));
 }
-// Same for a plain FP32 value x.
-__device__ __forceinline__ uint32_t round_u8(float x) {
-    const float t = __saturatef(x * (1.0f / 255.0f));
-    return __float_as_uint(__fmaf_rn(t, 255.0f, 12582912.0f));
-}
-// Pack the low bytes of four words.
-__device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    return __byte_perm(__byte_perm(a, b, 0x0040u), __byte_perm(c, d, 0x0040u), 0x5410u);
+// q_of(x): nearest integer of a plain FP32 value, ties to even.
+__device__ __forceinline__ int q_of(float x) { return __float_as_int(__fmul_rn(x, 0x1p-149f)); }
+// Four int32 values saturated to [0, 255], packed low byte first.
+__device__ __forceinline__ uint32_t pack4_sat(int q0, int q1, int q2, int q3) {
+    uint32_t hi, w;
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(hi) : "r"(q3), "r"(q2), "r"(0));
+    asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(w) : "r"(q1), "r"(q0), "r"(hi));
+    return w;
 }
 
 }  // namespace rdct

@@ -7,6 +7,8 @@ namespace rdct {
 
 cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps,
                                 cudaStream_t s) {
+    if (kind == RDCT_KIND_RDCT && !job.dstf)
+        return launch_fused2_single(job, reinterpret_cast<unsigned long long *>(acc), ctas_per_sm, 4, s);
     const int d = diag_class_host(job.r);
     const int64_t items = (int64_t)job.nbh * job.segs;
     const int out = (job.dst ? 1 : 0) | (job.dstf ? 2 : 0);
@@ -29,13 +31,17 @@ cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int cta
 #undef RDCT_SINGLE
 }
 
-int batch_class_of_diag(int d) { return d <= 5 ? 0 : (d <= 8 ? 1 : 2); }
+int batch_group_of_diag(int d, int blocks_per_thread) {
+    if (blocks_per_thread == 2) return d;
+    return d <= 5 ? 0 : (d <= 8 ? 1 : 2);
+}
 
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
-                               int cls, int ctas_per_sm, int warps, cudaStream_t s) {
+                               int group, int ctas_per_sm, int warps, int blocks_per_thread, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
-    if (cls == 0) launch_persistent(fused_batch_kernel<1, 0, 5>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
-    else if (cls == 1) launch_persistent(fused_batch_kernel<1, 6, 8>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
+    if (blocks_per_thread == 2) return launch_fused2_batch(jobs, chunks, nchunks, acc_u64, group, ctas_per_sm, s);
+    if (group == 0) launch_persistent(fused_batch_kernel<1, 0, 5>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
+    else if (group == 1) launch_persistent(fused_batch_kernel<1, 6, 8>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
     else launch_persistent(fused_batch_kernel<1, 9, 14>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
     return cudaGetLastError();
 }

@@ -1,0 +1,367 @@
+// rdct_fused2.cuh -- the fused RDCT kernel (Sec. 3 of Cintra & Bayer: forward
+// transform, zonal truncation with the S scaling of Sec. 2, inverse, squared
+// error) shaped for sm_103a issue rates.
+//
+// Per 8x8 block, one thread:
+//   * rows of pixels arrive through a per-thread cp.async ring in shared
+//     memory (three stages in flight, no block barriers: each thread only
+//     reads what it copied itself);
+//   * row pass: every output of C0 applied to a row is one pair of byte dot
+//     products (dp4a) of the packed pixels with a row of C0 as signed bytes,
+//     so pixels are never unpacked;
+//   * column pass: the 22-addition C0 butterfly in int32; the compiler drops
+//     every output that r never keeps;
+//   * compression: kept coefficients become Z = W Y with W = 576 d_i^2 d_j^2,
+//     converted exactly to FP32 in units of 2^-149 (subnormal range);
+//   * inverse: C0^T butterflies in FP32, exact because every value is an
+//     integer multiple of 2^-149 below 2^24 units; the row pass runs on
+//     packed pairs of rows (f32x2);
+//   * output: one f32x2 multiply by 1/576 leaves round(Xhat) in the bit
+//     pattern of each float (negative values carry the sign bit), and
+//     cvt.pack.sat clamps to [0, 255] and packs four pixels per two
+//     instructions;
+//   * error: 576 SSE = 576 sum x^2 - sum_kept W Y^2 (Parseval, the transform
+//     is orthogonal), with sum x^2 from dp4a and the kept energies summed
+//     per weight group in 32 bits: exact.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rdct_blocks.cuh"
+
+namespace rdct {
+
+// ------------------------------------------------------------ f32x2 pairs
+
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_split(f2 r, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r.v));
+}
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 operator-(f2 a) { return f2{0ull} - a; }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+
+// ------------------------------------------------------------ int helpers
+
+// a (four unsigned bytes) . b (four signed bytes) + c
+__device__ __forceinline__ int dp4a_us(unsigned a, unsigned b, int c) {
+    int d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// Weight group of W_ij (six distinct values).
+__host__ __device__ constexpr int weight_group(int i, int j) {
+    const int w = weight(i, j);
+    return w == 9 ? 0 : w == 12 ? 1 : w == 16 ? 2 : w == 18 ? 3 : w == 24 ? 4 : 5;
+}
+__host__ __device__ constexpr int group_weight(int g) {
+    return g == 0 ? 9 : g == 1 ? 12 : g == 2 ? 16 : g == 3 ? 18 : g == 4 ? 24 : 36;
+}
+
+// --------------------------------------------------------------- block body
+
+// One 8x8 block in rows w[0..7] (8 pixels each, little-endian); keeps every
+// anti-diagonal < D plus the ranks < r of diagonal D.  Writes the uint8
+// reconstruction when dst != nullptr; returns 576 * SSE of the block.
+template <int D>
+__device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], int r, uint8_t *dst,
+                                                           int64_t dpitch, int dalign) {
+    unsigned sumsq = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        sumsq = __dp4a(w[i].x, w[i].x, sumsq);
+        sumsq = __dp4a(w[i].y, w[i].y, sumsq);
+    }
+    // row pass: R[i][k] = sum_n C0[k][n] A[i][n]
+    int R[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            R[i][k] = dp4a_us(w[i].x, c0_row_word(k, 0), dp4a_us(w[i].y, c0_row_word(k, 1), 0));
+    // column pass: Y = C0 R
+    int Y[8][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int c[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
+        c0_forward(c, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Y[i][j] = o[i];
+    }
+    // compression: Z = W Y on the retained zone, as FP32 in units of 2^-149
+    unsigned g2[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    float Z[8][8];
+    static_for<0, 8>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        static_for<0, 8>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            if constexpr (i + j <= D) {
+                int y = Y[i][j];
+                if constexpr (i + j == D) {
+                    if (zz_rank(i, j) >= r) y = 0;
+                }
+                g2[weight_group(i, j)] += (unsigned)(y * y);
+                // bits of 1.5 * 2^23 + W y; the fma rescales by 2^-149 exactly
+                const int zb = y * weight(i, j) + 0x4B400000;
+                Z[i][j] = __fmaf_rn(__int_as_float(zb), 0x1p-149f, -0x1.8p-126f);
+            } else {
+                Z[i][j] = 0.0f;
+            }
+        });
+    });
+    unsigned long long kept = 0;
+#pragma unroll
+    for (int g = 0; g < 6; ++g) kept += (unsigned long long)g2[g] * (unsigned)group_weight(g);
+
+    if (dst != nullptr) {
+        // inverse columns: U = C0^T Z (scalar FP32)
+        float U[8][8];
+        static_for<0, 8>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            constexpr unsigned m = col_mask(D, j);
+            if constexpr (m != 0u) {
+                float in[8], out[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) in[i] = Z[i][j];
+                c0t_inverse<m>(in, out);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) U[i][j] = out[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) U[i][j] = 0.0f;
+            }
+        });
+        // inverse rows two at a time (f32x2), then round, clamp, pack, store
+        constexpr unsigned rm = row_mask(D);
+        const f2 inv576 = f2_make(1.0f / 576.0f, 1.0f / 576.0f);
+#pragma unroll
+        for (int n = 0; n < 8; n += 2) {
+            f2 in[8], E[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) in[j] = f2_make(U[n][j], U[n + 1][j]);
+            c0t_inverse<rm>(in, E);
+            int qa[8], qb[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                float a, b;
+                f2_split(mul2(E[m], inv576), a, b);
+                qa[m] = __float_as_int(a);
+                qb[m] = __float_as_int(b);
+            }
+            store_row_u8(dst + n * dpitch, dalign, pack4_sat(qa[0], qa[1], qa[2], qa[3]),
+                         pack4_sat(qa[4], qa[5], qa[6], qa[7]));
+            store_row_u8(dst + (n + 1) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
+                         pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+        }
+    }
+    return 576ull * (unsigned long long)sumsq - kept;
+}
+
+// ------------------------------------------------------------------ kernel
+
+// Launch shape per anti-diagonal class: registers grow with the retained zone,
+// so small classes run more warps per SM.
+template <int D>
+struct Fused2Shape {
+    static constexpr int threads = 128;
+    static constexpr int min_blocks = D <= 4 ? 6 : (D == 5 ? 5 : (D <= 8 ? 4 : 3));
+};
+constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
+constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
+
+__device__ __forceinline__ void cp_async8(uint32_t smem_addr, const void *gptr) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Work description shared by the single-plane and batch launches.  A strip
+// (work item) is kVRows block rows by 32 blocks; item t of a plane is
+// strip-row t / segs, segment t % segs.
+struct Fused2Args {
+    const JobDesc *jobs;       // batch: device job table; single: unused
+    const Chunk *chunks;       // batch: device chunk table; single: unused
+    int32_t nchunks;
+    int32_t chunk_items;       // single: strips per virtual chunk
+    unsigned long long *acc;   // batch: per-image 576*SSE; single: one slot
+    JobDesc single;            // single-plane job (by value)
+};
+
+template <bool SINGLE>
+__device__ __forceinline__ Chunk get_chunk(const Fused2Args &a, int c) {
+    if constexpr (SINGLE) {
+        const int total = ((a.single.nbh + kVRows - 1) / kVRows) * a.single.segs;
+        const int it0 = c * a.chunk_items;
+        const int n = total - it0 < a.chunk_items ? total - it0 : a.chunk_items;
+        return Chunk{0, it0, n, diag_class(a.single.r)};
+    } else {
+        return a.chunks[c];
+    }
+}
+template <bool SINGLE>
+__device__ __forceinline__ const JobDesc &get_job(const Fused2Args &a, int j) {
+    if constexpr (SINGLE) return a.single;
+    else return a.jobs[j];
+}
+
+// Walks the strips of one warp: chunks c = warp, warp + nwarps, ...; inside a
+// chunk the strips advance segment by segment without divisions.
+struct Cursor {
+    int c, by, seg, left, job, diag;
+};
+template <bool SINGLE>
+__device__ __forceinline__ void cursor_load(const Fused2Args &a, Cursor &cu) {
+    if (cu.c < a.nchunks) {
+        const Chunk ch = get_chunk<SINGLE>(a, cu.c);
+        const int segs = get_job<SINGLE>(a, ch.job).segs;
+        const int g = ch.item0 / segs;
+        cu.by = g * kVRows;
+        cu.seg = ch.item0 - g * segs;
+        cu.left = ch.nitems;
+        cu.job = ch.job;
+        cu.diag = ch.diag;
+    }
+}
+template <bool SINGLE>
+__device__ __forceinline__ void cursor_next(const Fused2Args &a, Cursor &cu, int nwarps) {
+    if (--cu.left > 0) {
+        if (++cu.seg == get_job<SINGLE>(a, cu.job).segs) {
+            cu.seg = 0;
+            cu.by += kVRows;
+        }
+    } else {
+        cu.c += nwarps;
+        cursor_load<SINGLE>(a, cu);
+    }
+}
+
+// Copy this lane's blocks of a strip into ring stage `st` (rows of block v at
+// ring rows 8v .. 8v+7).
+template <int THREADS>
+__device__ __forceinline__ void fetch_strip(const JobDesc &job, int by, int seg, int lane, uint2 *ring, int st) {
+    const int bx = seg * 32 + lane;
+    if (bx < job.nbw) {
+        const int64_t pitch = job.src_pitch;
+        const uint8_t *src = job.src + (int64_t)by * 8 * pitch + (int64_t)bx * 8;
+        uint2 *dst = ring + st * 8 * kVRows * THREADS + threadIdx.x;
+        const int rows = (job.nbh - by) >= kVRows ? 8 * kVRows : 8 * (job.nbh - by);
+        if (job.align >= 8) {
+            const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(dst);
+#pragma unroll
+            for (int i = 0; i < 8 * kVRows; ++i) {
+                if (i < rows) cp_async8(s0 + i * THREADS * 8, src);
+                src += pitch;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8 * kVRows; ++i) {
+                if (i < rows) {
+                    uint2 v;
+                    v.x = (uint32_t)src[0] | ((uint32_t)src[1] << 8) | ((uint32_t)src[2] << 16) |
+                          ((uint32_t)src[3] << 24);
+                    v.y = (uint32_t)src[4] | ((uint32_t)src[5] << 8) | ((uint32_t)src[6] << 16) |
+                          ((uint32_t)src[7] << 24);
+                    dst[i * THREADS] = v;
+                }
+                src += pitch;
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+// Persistent fused kernel: each lane owns kVRows vertically adjacent blocks of
+// every strip its warp visits; strips stream through a double-buffered
+// per-thread cp.async ring.  DLO..DHI are the anti-diagonal classes compiled in
+// (one class for single-plane launches).
+template <int DLO, int DHI, bool SINGLE, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args a) {
+    __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+
+    Cursor fc{gw, 0, 0, 0, 0, 0};
+    cursor_load<SINGLE>(a, fc);
+    Cursor cc = fc;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (fc.c < a.nchunks) {
+            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.by, fc.seg, lane, ring, s);
+            cursor_next<SINGLE>(a, fc, nwarps);
+        } else {
+            cp_async_commit();
+        }
+    }
+    unsigned long long s576 = 0;
+    int stage = 0;
+    while (cc.c < a.nchunks) {
+        cp_async_wait<kStages - 2>();
+        const JobDesc &job = get_job<SINGLE>(a, cc.job);
+        const int bx = cc.seg * 32 + lane;
+        const int nblk = bx < job.nbw ? (job.nbh - cc.by >= kVRows ? kVRows : job.nbh - cc.by) : 0;
+        const int refill = stage == 0 ? kStages - 1 : stage - 1;
+        if (fc.c < a.nchunks) {
+            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.by, fc.seg, lane, ring, refill);
+            cursor_next<SINGLE>(a, fc, nwarps);
+        } else {
+            cp_async_commit();
+        }
+        uint8_t *dst = job.dst ? job.dst + (int64_t)cc.by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
+        const int r = job.r;
+        const int64_t dpitch = job.dst_pitch;
+        const int dalign = job.dalign;
+        // blocks one after the other (the refill above went to the other stage)
+#pragma unroll 1
+        for (int v = 0; v < kVRows; ++v) {
+            if (v < nblk) {
+                uint2 w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
+                static_for<DLO, DHI + 1>([&](auto dc) {
+                    constexpr int d = decltype(dc)::value;
+                    if (cc.diag == d) s576 += fused2_block<d>(w, r, dst, dpitch, dalign);
+                });
+            }
+            if (dst) dst += 8 * dpitch;
+        }
+        stage = stage + 1 == kStages ? 0 : stage + 1;
+        const int img = job.image;
+        const int cprev = cc.c;
+        cursor_next<SINGLE>(a, cc, nwarps);
+        if (cc.c != cprev) {  // end of a chunk: one atomic per warp
+            const unsigned long long t = warp_sum_u64(s576);
+            if (lane == 0 && t) atomicAdd(SINGLE ? a.acc : a.acc + img, t);
+            s576 = 0;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace rdct

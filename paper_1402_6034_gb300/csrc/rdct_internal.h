@@ -24,6 +24,11 @@ struct JobDesc {
     int32_t pad;
 };
 
+// The fused kernel takes strips of kFusedVRows block rows (one thread owns
+// that many vertically adjacent blocks); the scalar kernel strips of one.
+constexpr int kFusedVRows = 2;
+inline int32_t strips_of(const JobDesc &j, int vrows) { return ((j.nbh + vrows - 1) / vrows) * j.segs; }
+
 // A run of consecutive strips of one job handed to one warp.
 struct Chunk {
     int32_t job, item0, nitems, diag;
@@ -70,13 +75,22 @@ cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double 
 // Fused path for one job: acc is the caller's SSE slot (zeroed by the caller),
 // used as uint64 576*SSE for kind RDCT and as double SSE for kind DCT.
 cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps, cudaStream_t s);
-// Persistent batch kernel over the chunks of one register class
-// (batch_class_of_diag); acc_u64[image] += 576 * SSE.  ctas_per_sm <= 0 uses
-// the occupancy limit.
-int batch_class_of_diag(int d);
-constexpr int kBatchClasses = 3;
+// Persistent batch kernels.  Chunks are grouped: with blocks_per_thread 2
+// one group per anti-diagonal class of r (15 groups, one specialised kernel
+// each), with blocks_per_thread 1 one group per register class (3 groups).
+// acc_u64[image] += 576 * SSE.  ctas_per_sm <= 0 uses the occupancy limit.
+constexpr int kBatchGroups = 15;
+int batch_group_of_diag(int d, int blocks_per_thread);
+// blocks_per_thread 2 selects the dp4a/f32x2 kernel (128 threads per CTA,
+// strips of kFusedVRows block rows), 1 the scalar kernel with `warps` warps.
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
-                               int cls, int ctas_per_sm, int warps, cudaStream_t s);
+                               int group, int ctas_per_sm, int warps, int blocks_per_thread, cudaStream_t s);
+// The fused kernel for sm_103a issue rates (dp4a row pass, f32x2 inverse,
+// cp.async ring): uint8 output or error only, any alignment.
+cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, int ctas_per_sm, int chunk_items,
+                                 cudaStream_t s);
+cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
+                                int d, int ctas_per_sm, cudaStream_t s);
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).

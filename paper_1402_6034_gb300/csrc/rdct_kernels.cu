@@ -144,7 +144,10 @@ __global__ void __launch_bounds__(256) inverse_kernel(const float *__restrict__ 
             if (u8) {
                 uint8_t *p = u8 + row * pitch + bx * 8;
 #pragma unroll
-                for (int m = 0; m < 8; ++m) p[m] = (uint8_t)round_u8(X[m]);
+                for (int m = 0; m < 8; ++m) {
+                    const int q = q_of(X[m]);
+                    p[m] = (uint8_t)(q < 0 ? 0 : (q > 255 ? 255 : q));
+                }
             }
             if (f32) {
                 float *p = f32 + row * pitch_f32 + bx * 8;

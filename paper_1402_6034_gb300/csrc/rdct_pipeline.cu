@@ -193,15 +193,13 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
             const rdct_host_job &j = jobs[b.job];
             rdct_plane pl{s.d_in + b.off, j.w, j.w, b.rows};
             JobDesc d = make_job(pl, j.dst ? s.d_out + b.off : nullptr, j.w, nullptr, 0, j.r, j.image, 1);
-            const int items = d.nbh * d.segs;
+            const int items = strips_of(d, kFusedVRows);
             const int diag = diag_class_host(j.r);
             for (int it = 0; it < items; it += kItemsPerChunk)
                 cd.push_back(Chunk{(int32_t)jd.size(), it, std::min(kItemsPerChunk, items - it), diag});
             jd.push_back(d);
         }
-        std::stable_sort(cd.begin(), cd.end(), [](const Chunk &a, const Chunk &b) {
-            return batch_class_of_diag(a.diag) < batch_class_of_diag(b.diag);
-        });
+        std::stable_sort(cd.begin(), cd.end(), [](const Chunk &a, const Chunk &b) { return a.diag < b.diag; });
         rdct_status st = ensure_tables(s, (int32_t)jd.size(), (int32_t)cd.size());
         if (st) return st;
         std::memcpy(s.h_jobs, jd.data(), jd.size() * sizeof(JobDesc));
@@ -216,11 +214,11 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         RDCT_CUDA_TRY(cudaEventRecord(s.in_ready, p->h2d));
         RDCT_CUDA_TRY(cudaStreamWaitEvent(p->comp, s.in_ready, 0));
         int32_t begin = 0;
-        for (int c = 0; c < kBatchClasses; ++c) {
+        for (int c = 0; c < kBatchGroups; ++c) {
             int32_t end = begin;
-            while (end < (int32_t)cd.size() && batch_class_of_diag(cd[end].diag) == c) ++end;
+            while (end < (int32_t)cd.size() && cd[end].diag == c) ++end;
             if (end > begin)
-                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 8, p->comp));
+                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2, p->comp));
             begin = end;
         }
         RDCT_CUDA_TRY(cudaEventRecord(s.computed, p->comp));

@@ -113,8 +113,16 @@ _SIGS = {
     "rdct_server_cancel": [_vp, ctypes.c_uint64],
     "rdct_server_stats_get": [_vp, ctypes.POINTER(ServerStats)],
     "rdct_server_destroy": [_vp],
+    "rdct_server_inject_alloc_failures": [_vp, _i32],
+    "rdct_arena_create": [_i64, _i64, ctypes.POINTER(_vp)],
+    "rdct_arena_alloc": [_vp, _i64, ctypes.POINTER(_i64)],
+    "rdct_arena_free": [_vp, _i64],
+    "rdct_arena_used": [_vp],
+    "rdct_arena_largest_free": [_vp],
+    "rdct_arena_destroy": [_vp],
 }
-_RESTYPE = {"rdct_status_string": ctypes.c_char_p, "rdct_last_error": ctypes.c_size_t, "rdct_version": ctypes.c_int32}
+_RESTYPE = {"rdct_status_string": ctypes.c_char_p, "rdct_last_error": ctypes.c_size_t, "rdct_version": ctypes.c_int32,
+            "rdct_arena_used": ctypes.c_int64, "rdct_arena_largest_free": ctypes.c_int64}
 
 
 def lib_path() -> str:
@@ -350,3 +358,156 @@ def autotune(jobs: list[BatchJob], nimages: int, stream=None) -> dict:
     t = Tune()
     _check(load().rdct_autotune(arr, len(jobs), nimages, ctypes.byref(t), _stream(stream)), "rdct_autotune")
     return t.as_dict()
+
+
+# ---------------------------------------------------------- host streaming
+
+class Pipeline:
+    """Planes in host memory streamed through the fused path (copies overlapped with kernels)."""
+
+    def __init__(self, device_budget_bytes: int = 1 << 30, depth: int = 3):
+        h = ctypes.c_void_p()
+        _check(load().rdct_pipeline_create(device_budget_bytes, depth, ctypes.byref(h)), "rdct_pipeline_create")
+        self._h = h
+
+    def run(self, jobs: list[tuple], nimages: int):
+        """jobs: (src, dst or None, r, image) with src/dst 2-D uint8 host arrays (numpy or CPU tensors)."""
+        arr = (HostJob * len(jobs))()
+        keep = []
+        for i, (src, dst, r, image) in enumerate(jobs):
+            sp, pitch, h, w = _host_ptr(src)
+            dp = _host_ptr(dst)[0] if dst is not None else None
+            arr[i] = HostJob(sp, dp, pitch, w, h, r, image)
+            keep.append((src, dst))
+        sse = (ctypes.c_double * max(nimages, 1))()
+        _check(load().rdct_pipeline_run(self._h, arr, len(jobs), nimages, sse), "rdct_pipeline_run")
+        return list(sse[:nimages])
+
+    def close(self):
+        if self._h:
+            load().rdct_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    """(address, pitch, h, w) of a 2-D (or [planes, h, w]) uint8 host array with unit column stride."""
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.uint8 or a.stride(-1) != 1:
+            raise ValueError("host plane must be a CPU uint8 tensor with unit column stride")
+        return a.data_ptr(), a.stride(-2), a.shape[-2], a.shape[-1]
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.uint8 or a.strides[-1] != 1:
+        raise ValueError("host plane must be a uint8 numpy array with unit column stride")
+    return a.ctypes.data, a.strides[-2], a.shape[-2], a.shape[-1]
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """Continuous-batching server; requests are host images [planes, h, w] (uint8)."""
+
+    def __init__(self, device_budget_bytes: int = 8 << 30, max_batch: int = 64, queue_capacity: int = 4096,
+                 streams: int = 2, max_wait_us: int = 0):
+        opts = ServerOpts(device_budget_bytes, max_batch, queue_capacity, streams, max_wait_us)
+        h = ctypes.c_void_p()
+        _check(load().rdct_server_create(ctypes.byref(opts), ctypes.byref(h)), "rdct_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, src, r: int, dst=None) -> int:
+        """Queue an image; src/dst are host uint8 arrays [planes, h, w] (contiguous planes)."""
+        if src.ndim == 2:
+            src = src[None]
+            dst = dst[None] if dst is not None else None
+        sp, pitch, h, w = _host_ptr(src)
+        dp = _host_ptr(dst)[0] if dst is not None else None
+        req = Request(sp, dp, pitch, w, h, src.shape[0], r)
+        t = ctypes.c_uint64()
+        _check(load().rdct_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "rdct_server_submit")
+        self._keep[t.value] = (src, dst)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        res = Result()
+        st = load().rdct_server_wait(self._h, ticket, timeout_us, ctypes.byref(res))
+        if st != 6:  # keep buffers alive while still pending
+            self._keep.pop(ticket, None)
+        _check(st, "rdct_server_wait")
+        return {"sse": res.sse, "mse": res.mse, "psnr": res.psnr, "latency_us": res.latency_us}
+
+    def poll(self, ticket: int):
+        res = Result()
+        st = load().rdct_server_poll(self._h, ticket, ctypes.byref(res))
+        if st == 7:
+            return None
+        self._keep.pop(ticket, None)
+        _check(st, "rdct_server_poll")
+        return {"sse": res.sse, "mse": res.mse, "psnr": res.psnr, "latency_us": res.latency_us}
+
+    def cancel(self, ticket: int):
+        _check(load().rdct_server_cancel(self._h, ticket), "rdct_server_cancel")
+
+    def inject_alloc_failures(self, n: int):
+        _check(load().rdct_server_inject_alloc_failures(self._h, n), "rdct_server_inject_alloc_failures")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().rdct_server_stats_get(self._h, ctypes.byref(st)), "rdct_server_stats_get")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(load().rdct_server_destroy(self._h), "rdct_server_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Arena:
+    """The server's offset sub-allocator (host logic only; usable without a GPU)."""
+
+    def __init__(self, size: int, align: int = 256):
+        h = ctypes.c_void_p()
+        _check(load().rdct_arena_create(size, align, ctypes.byref(h)), "rdct_arena_create")
+        self._h = h
+
+    def alloc(self, nbytes: int):
+        off = ctypes.c_int64()
+        st = load().rdct_arena_alloc(self._h, nbytes, ctypes.byref(off))
+        if st == 3:
+            return None
+        _check(st, "rdct_arena_alloc")
+        return off.value
+
+    def free(self, off: int):
+        _check(load().rdct_arena_free(self._h, off), "rdct_arena_free")
+
+    @property
+    def used(self) -> int:
+        return load().rdct_arena_used(self._h)
+
+    @property
+    def largest_free(self) -> int:
+        return load().rdct_arena_largest_free(self._h)
+
+    def close(self):
+        if self._h:
+            load().rdct_arena_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
