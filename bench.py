@@ -37,13 +37,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["video", "batch512"], default="video")
+    ap.add_argument("--workload", choices=["video", "batch512", "uneven", "sweep"], default="video")
     ap.add_argument("--frames", type=int, default=600)
     ap.add_argument("--r", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -61,6 +63,26 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- multi-rank
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest value over all ranks (the slowest rank's time); x itself on one rank.
+    Ends with a barrier so no rank starts later work before the others finished timing."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def weak_scaling_value(samples_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job Gpixel/s: every rank processed its own copy of the workload `steps` times; the
+    job took as long as the slowest rank."""
+    return world * samples_per_rank * steps / (ms_max / 1000.0) / 1e9
 
 
 # ------------------------------------------------------------------ clocks
@@ -229,6 +251,178 @@ def cpu_oracle_rate(planes_iter, r: int, budget_s: float):
     return done / t_total / 1e9, threads, done, t_total
 
 
+# ------------------------------------------------------- uneven / sweep modes
+
+def events_time(fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_uneven(args, dev):
+    """4096 images, sides uniform over multiples of 8 in [64, 2048], 1 or 3 planes, r from {4, 10, 16, 32}:
+    one graph-captured launch per step (autotuned) vs one plain launch per plane."""
+    from paper_1402_6034_gb300 import rdct, synth
+    n = 4096
+    specs = synth.uneven_specs(n, seed=0)
+    pool = synth.field_u8_torch(2048, 2048, 2.0, 0, device=str(dev), planes=4)
+    rng = np.random.Generator(np.random.PCG64(1))
+    sizes = [sp.w * sp.h for sp in specs for _ in range(sp.planes)]
+    total = sum(sizes)
+    src_buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    dst_buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    jobs, off = [], 0
+    for i, sp in enumerate(specs):
+        for p in range(sp.planes):
+            k = int(rng.integers(0, 4))
+            y0, x0 = int(rng.integers(0, 2048 - sp.h + 1)), int(rng.integers(0, 2048 - sp.w + 1))
+            src = src_buf[off:off + sp.w * sp.h].view(sp.h, sp.w)
+            src.copy_(pool[k, y0:y0 + sp.h, x0:x0 + sp.w])
+            jobs.append(rdct.BatchJob(src, dst_buf[off:off + sp.w * sp.h].view(sp.h, sp.w), sp.r, i))
+            off += sp.w * sp.h
+    tune = rdct.autotune(jobs, n)
+    plan = rdct.BatchPlan(jobs, n, tune=tune)
+    sse_g = torch.empty(n, dtype=torch.float64, device=dev)
+    sse_p = torch.empty(n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ms_graph = events_time(lambda: plan.run(sse_g, stream), args.steps, args.warmup, stream)
+    ms_plain = events_time(lambda: plan.run_per_plane(sse_p, stream), max(3, args.steps // 10), 2, stream)
+    identical = bool(torch.equal(sse_g, sse_p))
+    npix = torch.tensor([sp.w * sp.h * sp.planes for sp in specs], dtype=torch.float64, device=dev)
+    psnr = 10 * torch.log10(255.0 ** 2 / (sse_g / npix))
+    peak, kind = peaks()
+    alg = 2 * total + 8 * n
+    nclass = len({synth_diag(sp.r) for sp in specs})
+    return {"metric": METRIC, "value": total / (ms_graph / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "uneven_4096_images_64to2048_r4-10-16-32", "images": n, "planes": len(jobs),
+                       "samples_per_step": total, "tune": tune,
+                       "l2": f"inputs and outputs (2 x {total / 1e9:.2f} GB) larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms_graph / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms_graph / 1e3) / 1e9 / peak, "traffic": None,
+                         "peak_source": f"{kind} hbm_gbs"},
+            "gpu_launches": (nclass + 1) * args.steps,
+            "per_plane_launches": {"value": total / (ms_plain / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms_plain,
+                                   "launches_per_step": len(jobs) + 1},
+            "batched_over_per_plane": ms_plain / ms_graph, "sse_identical": identical,
+            "quality": {"mean_psnr_db": float(psnr.mean())}}
+
+
+def synth_diag(r):
+    """Anti-diagonal class of r (the diagonal holding zigzag rank r - 1)."""
+    k, s, before = r - 1, 0, 0
+    while True:
+        ln = s + 1 if s < 8 else 15 - s
+        if k < before + ln:
+            return s
+        before += ln
+        s += 1
+
+
+def bench_sweep(args, dev):
+    """1024 images of 512 x 512, r = 1..64 for the RDCT and the exact DCT: one energy pass per transform
+    (rdct_sweep), per-r average MSE / PSNR and the MSE absolute percentage error against the DCT."""
+    from paper_1402_6034_gb300 import rdct, synth
+    n = 1024
+    base = torch.from_numpy(synth.image_batch(64, 512, 512, 2.0, 0)).to(dev)
+    imgs = torch.cat([torch.roll(base, shifts=(8 * k, 8 * ((k * 7) % 64)), dims=(1, 2)) for k in range(n // 64)])
+    planes = rdct.plane_array(imgs)
+    out_r = torch.empty((n, 64), dtype=torch.float64, device=dev)
+    out_d = torch.empty((n, 64), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        rdct.sweep_noalloc(planes, out_r, rdct.KIND_RDCT, stream)
+        rdct.sweep_noalloc(planes, out_d, rdct.KIND_DCT, stream)
+
+    ms = events_time(step, args.steps, args.warmup, stream)
+    mse_r = (out_r / (512 * 512)).mean(0).cpu().numpy()
+    mse_d = (out_d / (512 * 512)).mean(0).cpu().numpy()
+    ps_r = (10 * torch.log10(255.0 ** 2 / (out_r / (512 * 512)))).cpu().numpy()
+    ps_d = (10 * torch.log10(255.0 ** 2 / (out_d / (512 * 512)))).cpu().numpy()
+    rows = {}
+    for r in (1, 5, 10, 16, 32, 45, 63):
+        rows[str(r)] = {"psnr_rdct": float(np.mean(ps_r[:, r - 1])), "psnr_dct": float(np.mean(ps_d[:, r - 1])),
+                        "mse_rdct": float(mse_r[r - 1]), "mse_dct": float(mse_d[r - 1]),
+                        "mse_ape_pct": float(100 * abs(mse_r[r - 1] - mse_d[r - 1]) / mse_d[r - 1])}
+    total = n * 512 * 512 * 2  # two transforms per step
+    peak, kind = peaks()
+    return {"metric": METRIC, "value": total / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32+fp32", "data": "synthetic",
+            "config": {"workload": "sweep_1024x512x512_r1-64_rdct_and_dct", "images": n,
+                       "samples_per_step": total, "note": "one pass per transform, 1 B/px read"},
+            "roofline": {"bound": "hbm", "achieved": total / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": total / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{kind} hbm_gbs"},
+            "gpu_launches": 6 * args.steps, "per_r": rows}
+
+
+# ------------------------------------------------------------------ serving
+
+def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0), seed: int = 0):
+    """Poisson arrivals of images (side log-uniform 256..4096, 1 or 3 planes, r ~ U{1..64}) against
+    the continuous-batching server and against one launch per image (max_batch 1, one stream).
+    Rate 0 submits everything at once (saturation).  Host buffers are pinned."""
+    from paper_1402_6034_gb300 import rdct, synth
+    pool = synth.field_u8_torch(4096, 4096, 2.0, seed, device=str(dev), planes=3).cpu()
+    trace = synth.poisson_trace(1.0, n_requests, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    reqs = []
+    for q in trace:
+        y0 = 8 * int(rng.integers(0, (4096 - q.side) // 8 + 1))
+        x0 = 8 * int(rng.integers(0, (4096 - q.side) // 8 + 1))
+        src = torch.empty((q.planes, q.side, q.side), dtype=torch.uint8).pin_memory()
+        src.copy_(pool[:q.planes, y0:y0 + q.side, x0:x0 + q.side])
+        dst = torch.empty((q.planes, q.side, q.side), dtype=torch.uint8).pin_memory()
+        reqs.append((src, dst, q.r, q.t))
+    samples = sum(s.numel() for s, _, _, _ in reqs)
+    # warm the library and the device once
+    w = rdct.Server(device_budget_bytes=1 << 28, max_batch=4, streams=1)
+    w.wait(w.submit(reqs[0][0], reqs[0][2], reqs[0][1]))
+    w.close()
+    rows = []
+    for rate in rates:
+        row = {"rate_req_s": rate if rate else "saturation"}
+        sses = {}
+        for name, kw in (("served", dict(max_batch=64, streams=2)), ("plain", dict(max_batch=1, streams=1))):
+            srv = rdct.Server(device_budget_bytes=8 << 30, queue_capacity=n_requests + 1, **kw)
+            t0 = time.perf_counter()
+            tickets = []
+            for src, dst, r, t in reqs:
+                if rate:
+                    target = t0 + t / rate
+                    while True:
+                        now = time.perf_counter()
+                        if now >= target:
+                            break
+                        if target - now > 2e-3:
+                            time.sleep(target - now - 1e-3)
+                tickets.append(srv.submit(src, r, dst))
+            res = [srv.wait(tk) for tk in tickets]
+            st = srv.stats()
+            srv.close()
+            sses[name] = [x["sse"] for x in res]
+            psnrs = [x["psnr"] for x in res if math.isfinite(x["psnr"])]
+            row[name] = {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                         "mean_ms": st["mean_us"] / 1e3, "gpixels_per_s": st["gpixels_per_s"],
+                         "launches": st["batches"], "mean_psnr_db": float(np.mean(psnrs)) if psnrs else None}
+        row["sse_identical"] = sses["served"] == sses["plain"]
+        rows.append(row)
+    return {"requests": n_requests, "samples": samples, "sides": "log-uniform 256..4096, square",
+            "planes": "1 or 3", "r": "uniform 1..64", "host_buffers": "pinned",
+            "served": "max_batch 64, 2 compute streams, 8 GiB device budget",
+            "plain": "one launch per image (max_batch 1, 1 stream), same admission and copies",
+            "latency": "submit to completion (C++ steady clock)", "rates": rows}
+
+
 # ---------------------------------------------------------------- reference
 
 def run_reference(args, rank, world):
@@ -290,6 +484,11 @@ def main():
     from paper_1402_6034_gb300 import rdct
     rdct.load()
 
+    if args.workload in ("uneven", "sweep"):
+        line = (bench_uneven if args.workload == "uneven" else bench_sweep)(args, dev)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     wl = (VideoWorkload if args.workload == "video" else Batch512Workload)(args.frames, args.r, dev)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -309,13 +508,7 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        dist.barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     time.sleep(0.3 if sampler else 0)
     clocks = sampler.summary(t0, t1) if sampler else None
     if sampler:
@@ -323,7 +516,7 @@ def main():
     quality = wl.quality()
 
     ms_step = ms / args.steps
-    value = world * wl.samples * args.steps / (ms / 1000.0) / 1e9
+    value = weak_scaling_value(wl.samples, args.steps, ms, world)
     peak, peak_kind = peaks()
     alg_bytes = 2 * wl.samples + 8 * wl.nimages
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
@@ -354,6 +547,9 @@ def main():
                        "api": "rdct_pipeline_run (pinned host buffers, copies overlapped with kernels)",
                        "sse_matches_device_path": ok}
         del bufs
+
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_bench(dev, args.serving_requests)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, done, tt = cpu_oracle_rate(wl.cpu_planes(), args.r, args.cpu_seconds)

@@ -244,12 +244,14 @@ typedef struct {
     int32_t max_wait_us;         /* how long a lone request may wait for company */
 } rdct_server_opts;
 
-/* A request: an image of `planes` planes (1 or 3), all w x h, packed
- * contiguously in host memory (plane p at src + p*pitch*h). */
+/* A request: an image of `planes` planes (1..4), all w x h, in host memory:
+ * plane p starts at src + p * plane_stride (plane_stride 0 means pitch * h),
+ * rows are `pitch` bytes apart; dst uses the same layout. */
 typedef struct {
     const uint8_t *src; /* host */
     uint8_t *dst;       /* host, receives the uint8 reconstruction (same layout), may be NULL */
     int64_t pitch;
+    int64_t plane_stride;
     int32_t w, h, planes, r;
 } rdct_request;
 

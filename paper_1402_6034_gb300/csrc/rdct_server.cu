@@ -109,6 +109,8 @@ rdct_status validate_request(const rdct_request *q) {
     if (q->w <= 0 || q->h <= 0 || q->w % 8 || q->h % 8 || q->pitch < q->w)
         return set_error(RDCT_ERR_SHAPE, "rdct_server_submit: sides must be positive multiples of 8, pitch >= w");
     if (q->r < 1 || q->r > 64) return set_error(RDCT_ERR_ARG, "rdct_server_submit: r must be in 1..64");
+    if (q->plane_stride != 0 && q->planes > 1 && q->plane_stride < q->pitch * (q->h - 1) + q->w)
+        return set_error(RDCT_ERR_ARG, "rdct_server_submit: planes overlap (plane_stride too small)");
     return RDCT_OK;
 }
 
@@ -195,7 +197,7 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
         const int64_t plane = (int64_t)r.q.w * r.q.h;
         uint8_t *out = S->d_pool + r.arena_off + r.q.planes * plane;
         for (int p = 0; p < r.q.planes; ++p)
-            RDCT_CUDA_TRY(cudaMemcpy2DAsync(r.q.dst + (int64_t)p * r.q.pitch * r.q.h, r.q.pitch, out + p * plane,
+            RDCT_CUDA_TRY(cudaMemcpy2DAsync(r.q.dst + p * r.q.plane_stride, r.q.pitch, out + p * plane,
                                             r.q.w, r.q.w, r.q.h, cudaMemcpyDeviceToHost, L.s));
     }
     RDCT_CUDA_TRY(cudaMemcpyAsync(L.h_acc, L.d_acc, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, L.s));
@@ -261,7 +263,7 @@ void scheduler(rdct_server *S) {
             const int64_t plane = (int64_t)r->q.w * r->q.h;
             cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming);
             for (int p = 0; p < r->q.planes; ++p)
-                cudaMemcpy2DAsync(S->d_pool + off + p * plane, r->q.w, r->q.src + (int64_t)p * r->q.pitch * r->q.h,
+                cudaMemcpy2DAsync(S->d_pool + off + p * plane, r->q.w, r->q.src + p * r->q.plane_stride,
                                   r->q.pitch, r->q.w, r->q.h, cudaMemcpyHostToDevice, S->copy);
             cudaEventRecord(r->copied, S->copy);
             S->ready.push_back(r);
@@ -380,6 +382,7 @@ rdct_status rdct_server_submit(rdct_server *S, const rdct_request *req, uint64_t
     if (st) return st;
     auto r = std::make_shared<Req>();
     r->q = *req;
+    if (r->q.plane_stride == 0) r->q.plane_stride = r->q.pitch * r->q.h;
     request_bytes(*req, &r->bytes);
     r->bytes = (r->bytes + 255) & ~(int64_t)255;
     std::lock_guard<std::mutex> lk(S->mu);

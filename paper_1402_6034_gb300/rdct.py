@@ -63,8 +63,9 @@ class ServerOpts(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("pitch", ctypes.c_int64), ("w", ctypes.c_int32),
-                ("h", ctypes.c_int32), ("planes", ctypes.c_int32), ("r", ctypes.c_int32)]
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("pitch", ctypes.c_int64),
+                ("plane_stride", ctypes.c_int64), ("w", ctypes.c_int32), ("h", ctypes.c_int32),
+                ("planes", ctypes.c_int32), ("r", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -274,14 +275,19 @@ def sweep_noalloc(planes, out: torch.Tensor, kind: int = KIND_RDCT, stream=None)
     memory at call time.  ``out`` is a caller-owned float64 [n, 64] CUDA tensor (allocated in
     advance).  At most 2048 planes / about 1.07 Gpixel per call; concurrent calls race on the
     library's fixed table storage and must be serialised by the caller."""
+    arr = planes if isinstance(planes, ctypes.Array) else plane_array(planes)
+    _require_cuda(out, "out", torch.float64)
+    if out.shape != (len(arr), 64) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [n, 64] float64 tensor")
+    _check(load().rdct_sweep_noalloc(arr, len(arr), kind, out.data_ptr(), _stream(stream)), "rdct_sweep_noalloc")
+    return out
+
+
+def plane_array(planes) -> ctypes.Array:
+    """rdct_plane[] for a list of 2-D uint8 CUDA tensors or a [n, h, w] tensor (build once, reuse)."""
     if isinstance(planes, torch.Tensor) and planes.dim() == 3:
         planes = list(planes.unbind(0))
-    _require_cuda(out, "out", torch.float64)
-    if out.shape != (len(planes), 64) or not out.is_contiguous():
-        raise ValueError("out must be a contiguous [n, 64] float64 tensor")
-    arr = (Plane * len(planes))(*[plane_of(t) for t in planes])
-    _check(load().rdct_sweep_noalloc(arr, len(planes), kind, out.data_ptr(), _stream(stream)), "rdct_sweep_noalloc")
-    return out
+    return (Plane * len(planes))(*[plane_of(t) for t in planes])
 
 
 def psnr_of_mse(mse):
@@ -421,13 +427,20 @@ class Server:
         self._keep = {}
 
     def submit(self, src, r: int, dst=None) -> int:
-        """Queue an image; src/dst are host uint8 arrays [planes, h, w] (contiguous planes)."""
+        """Queue an image; src/dst are host uint8 arrays [planes, h, w] (strided views allowed; dst must
+        have the same strides as src)."""
         if src.ndim == 2:
             src = src[None]
             dst = dst[None] if dst is not None else None
         sp, pitch, h, w = _host_ptr(src)
-        dp = _host_ptr(dst)[0] if dst is not None else None
-        req = Request(sp, dp, pitch, w, h, src.shape[0], r)
+        stride = src.stride(0) if isinstance(src, torch.Tensor) else src.strides[0]
+        dp = None
+        if dst is not None:
+            dp, dpitch, _, _ = _host_ptr(dst)
+            dstride = dst.stride(0) if isinstance(dst, torch.Tensor) else dst.strides[0]
+            if dpitch != pitch or (src.shape[0] > 1 and dstride != stride):
+                raise ValueError("dst must have the same row pitch and plane stride as src")
+        req = Request(sp, dp, pitch, stride if src.shape[0] > 1 else 0, w, h, src.shape[0], r)
         t = ctypes.c_uint64()
         _check(load().rdct_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "rdct_server_submit")
         self._keep[t.value] = (src, dst)

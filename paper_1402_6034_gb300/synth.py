@@ -159,3 +159,22 @@ def poisson_trace(rate: float, n: int, seed: int = 0, lo: int = 256, hi: int = 4
         side = int(8 * round(math.exp(rng.uniform(math.log(lo), math.log(hi))) / 8))
         out.append(Request(t, side, int(rng.choice([1, 3])), int(rng.integers(1, 65))))
     return out
+
+
+def field_u8_torch(h: int, w: int, alpha: float, seed: int, device: str = "cpu", planes: int = 1):
+    """[planes, h, w] uint8 1/f^alpha planes generated with torch on `device` (same recipe as
+    image_1f, torch's generator instead of numpy's; used for large pools)."""
+    import torch
+
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    out = torch.empty((planes, h, w), dtype=torch.uint8, device=device)
+    fy = torch.fft.fftfreq(h, device=device)[:, None]
+    fx = torch.fft.fftfreq(w, device=device)[None, :]
+    f = torch.hypot(fy, fx)
+    gain = torch.where(f > 0, f.clamp_min(1e-12) ** (-alpha / 2.0), torch.zeros_like(f))
+    for p in range(planes):
+        z = torch.randn((h, w), generator=g).to(device)
+        x = torch.fft.ifft2(torch.fft.fft2(z) * gain).real
+        lo, hi = x.min(), x.max()
+        out[p] = torch.round(255.0 * (x - lo) / (hi - lo)).to(torch.uint8)
+    return out
