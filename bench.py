@@ -30,6 +30,21 @@ sys.path.insert(0, ROOT)
 METRIC = "fused RDCT fwd+compress+inv Gpixel/s and % HBM peak; serving p50/p99 latency"
 UNIT = "Gpixel/s"
 
+# DRAM bytes (read + write) per sample of the fused kernel, from the ncu capture summarised in
+# profiles/fused_video_40x4k_r16_ncu.md.  Reported only while the kernel sources still hash to
+# the value they had when the counters were taken.
+FUSED_TRAFFIC = {"sources_sha256_16": "6b4505178af9d3de", "bytes_per_sample": 1.898}
+FUSED_SOURCES = ["rdct_fused2.cuh", "rdct_device.cuh", "rdct_blocks.cuh", "rdct_fused2_batch.cu"]
+
+
+def fused_sources_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in FUSED_SOURCES:
+        with open(os.path.join(ROOT, "paper_1402_6034_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -519,13 +534,17 @@ def main():
     value = weak_scaling_value(wl.samples, args.steps, ms, world)
     peak, peak_kind = peaks()
     alg_bytes = 2 * wl.samples + 8 * wl.nimages
+    traffic = None
+    if args.workload == "video" and fused_sources_hash() == FUSED_TRAFFIC["sources_sha256_16"]:
+        traffic = FUSED_TRAFFIC["bytes_per_sample"] * wl.samples
     achieved = alg_bytes / (ms_step / 1000.0) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": wl.config,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "fused_batch_kernel (graph step incl. SSE memset/finalize)",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "fused2_kernel (one graph step: SSE memset, kernel, SSE finalize)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": f"{peak_kind} hbm_gbs (copy)"},
             "gpu_launches": wl.kernels_per_step * args.steps, "clocks": clocks, "quality": quality}
 
