@@ -47,7 +47,7 @@ rdct_tune default_tune() {
     rdct_tune t{};
     t.warps_per_cta = 4;
     t.ctas_per_sm = 0;  // occupancy limit
-    t.items_per_chunk = 8;
+    t.items_per_chunk = 16;
     t.blocks_per_thread = 2;
     return t;
 }

@@ -8,7 +8,7 @@ namespace rdct {
 cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps,
                                 cudaStream_t s) {
     if (kind == RDCT_KIND_RDCT && !job.dstf)
-        return launch_fused2_single(job, reinterpret_cast<unsigned long long *>(acc), ctas_per_sm, 4, s);
+        return launch_fused2_single(job, reinterpret_cast<unsigned long long *>(acc), ctas_per_sm, 0, s);
     const int d = diag_class_host(job.r);
     const int64_t items = (int64_t)job.nbh * job.segs;
     const int out = (job.dst ? 1 : 0) | (job.dstf ? 2 : 0);

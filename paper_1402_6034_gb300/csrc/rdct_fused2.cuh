@@ -182,12 +182,13 @@ __device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], 
 
 // ------------------------------------------------------------------ kernel
 
-// Launch shape per anti-diagonal class: registers grow with the retained zone,
-// so small classes run more warps per SM.
+// Launch shape per anti-diagonal class: 128 registers (4 CTAs of 128 threads
+// per SM) up to r = 45, 168 above.  Measured: more registers for more
+// independent work per thread beat more resident warps.
 template <int D>
 struct Fused2Shape {
     static constexpr int threads = 128;
-    static constexpr int min_blocks = D <= 4 ? 6 : (D == 5 ? 5 : (D <= 8 ? 4 : 3));
+    static constexpr int min_blocks = D <= 8 ? 4 : 3;
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
@@ -337,8 +338,9 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
         const int r = job.r;
         const int64_t dpitch = job.dst_pitch;
         const int dalign = job.dalign;
-        // blocks one after the other (the refill above went to the other stage)
-#pragma unroll 1
+        // both blocks of the strip (the refill above went to the other stage); unrolled
+        // so that their independent work interleaves
+#pragma unroll
         for (int v = 0; v < kVRows; ++v) {
             if (v < nblk) {
                 uint2 w[8];

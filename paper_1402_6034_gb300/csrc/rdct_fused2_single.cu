@@ -1,4 +1,6 @@
 // Single-plane launches of the fused kernel (one anti-diagonal class each).
+#include <algorithm>
+
 #include "rdct_fused2.cuh"
 
 namespace rdct {
@@ -7,8 +9,12 @@ cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, in
                                  cudaStream_t s) {
     Fused2Args a{};
     a.single = job;
-    a.chunk_items = chunk_items > 0 ? chunk_items : 4;
     const int64_t items = (int64_t)((job.nbh + kVRows - 1) / kVRows) * job.segs;
+    if (chunk_items <= 0) {  // enough chunks for every resident warp, at most 16 strips each
+        const int64_t warps = (int64_t)sm_count() * 16;
+        chunk_items = (int)std::min<int64_t>(16, std::max<int64_t>(1, items / warps));
+    }
+    a.chunk_items = chunk_items;
     a.nchunks = (int32_t)((items + a.chunk_items - 1) / a.chunk_items);
     a.acc = acc;
     if (a.nchunks == 0) return cudaSuccess;
