@@ -155,7 +155,7 @@ RDCT_API rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind k
  * real-time loop where an allocation could stall or synchronise the device, a
  * plug-in whose host process forbids device allocation).  Same arguments and
  * results as rdct_sweep; the per-call descriptor tables live in one fixed
- * device array inside the library (about 720 KiB, held on every GPU that
+ * device array inside the library (672 KiB, held on every GPU that
  * loads the library until the process exits) and are built on the device.
  * Limits: at most 2048 planes and 32768 chunks of 16 strips (about 1.07
  * Gpixel) per call, else RDCT_ERR_TOO_LARGE and nothing is enqueued.

@@ -2,6 +2,7 @@
 // Cintra & Bayer): argument validation, constant set-up and launches.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -242,30 +243,24 @@ rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, doub
     if (kind != RDCT_KIND_RDCT && kind != RDCT_KIND_DCT) return set_error(RDCT_ERR_ARG, "rdct_sweep: bad kind");
     if (reinterpret_cast<uintptr_t>(sse_by_r) % 8) return set_error(RDCT_ERR_ARG, "rdct_sweep: misaligned output");
     if (n == 0) return RDCT_OK;
-    std::vector<JobDesc> jobs(n);
-    std::vector<Chunk> chunks;
-    const int per_chunk = 16;  // a lane's uint32 bins hold 16 blocks of the largest |Y|^2
+    int64_t nchunks = 0;
     for (int32_t i = 0; i < n; ++i) {
         rdct_status st = validate_plane(&planes[i], "rdct_sweep");
         if (st) return st;
-        jobs[i] = make_job(planes[i], nullptr, 0, nullptr, 0, 64, i, 1);
-        const int items = jobs[i].nbh * jobs[i].segs;
-        for (int it = 0; it < items; it += per_chunk)
-            chunks.push_back(Chunk{i, it, items - it < per_chunk ? items - it : per_chunk, 0});
+        nchunks += sweep_chunk_count(planes[i]);
     }
+    if (nchunks > INT32_MAX) return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep: too many strips in one call");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t jb = jobs.size() * sizeof(JobDesc), cb = chunks.size() * sizeof(Chunk);
+    const size_t jb = ((size_t)n * sizeof(JobDesc) + 255) & ~(size_t)255, cb = (size_t)nchunks * sizeof(Chunk);
     void *tables = nullptr;
     if (cudaMallocAsync(&tables, jb + cb, s) != cudaSuccess)
         return set_error(RDCT_ERR_OOM, "rdct_sweep: table allocation failed");
     JobDesc *jd = reinterpret_cast<JobDesc *>(tables);
     Chunk *cd = reinterpret_cast<Chunk *>(reinterpret_cast<char *>(tables) + jb);
-    cudaError_t e = cudaMemcpyAsync(jd, jobs.data(), jb, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cd, chunks.data(), cb, cudaMemcpyHostToDevice, s);
+    cudaError_t e = build_sweep_tables(planes, n, jd, cd, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sse_by_r, 0, (size_t)n * 64 * sizeof(double), s);
-    if (e == cudaSuccess) e = launch_sweep(jd, cd, (int32_t)chunks.size(), (int)kind, sse_by_r, n, s);
+    if (e == cudaSuccess) e = launch_sweep(jd, cd, (int32_t)nchunks, (int)kind, sse_by_r, n, s);
     if (e == cudaSuccess) e = launch_sweep_finalize(sse_by_r, n, (int)kind, s);
-    // pageable-memory copies above have been staged before cudaMemcpyAsync returned
     cudaError_t e2 = cudaFreeAsync(tables, s);
     if (e != cudaSuccess) return cuda_error(e, "rdct_sweep");
     if (e2 != cudaSuccess) return cuda_error(e2, "rdct_sweep: free");

@@ -27,7 +27,7 @@ struct JobDesc {
 // The fused kernel takes strips of kFusedVRows block rows (one thread owns
 // that many vertically adjacent blocks); the scalar kernel strips of one.
 constexpr int kFusedVRows = 2;
-inline int32_t strips_of(const JobDesc &j, int vrows) { return ((j.nbh + vrows - 1) / vrows) * j.segs; }
+__host__ __device__ inline int32_t strips_of(const JobDesc &j, int vrows) { return ((j.nbh + vrows - 1) / vrows) * j.segs; }
 
 // A run of consecutive strips of one job handed to one warp.
 struct Chunk {
@@ -93,7 +93,16 @@ cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_
                                 int d, int ctas_per_sm, cudaStream_t s);
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
-// Sweep: per-plane zigzag energy, then suffix sums into SSE(r).
+// Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are
+// runs of at most kSweepChunkStrips strips of kFusedVRows block rows.
+constexpr int kSweepChunkStrips = 8;
+cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
+                          cudaStream_t s);
+// Sweep tables built on the device from plane descriptors passed as kernel
+// parameters (batches of kSweepBuildBatch planes; no host-to-device copy).
+constexpr int kSweepBuildBatch = 1024;
+int64_t sweep_chunk_count(const rdct_plane &p);
+cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, cudaStream_t s);
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
                          int32_t nplanes, cudaStream_t s);
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s);

@@ -214,81 +214,39 @@ __global__ void mse_finalize_kernel(const unsigned long long *acc_u64, const dou
 
 // ------------------------------------------------------------------ sweep
 
-// Per chunk: a warp transforms up to 16 strips of one plane; each lane keeps
-// 64 per-position energy bins in registers, then the warp reduces them and
-// adds them to the plane's 64 zigzag-ordered bins.
-template <int KIND>
-__global__ void __launch_bounds__(128) sweep_kernel(const JobDesc *__restrict__ jobs,
-                                                    const Chunk *__restrict__ chunks, int nchunks, double *out,
-                                                    const DctConsts C) {
-    const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int c = warp; c < nchunks; c += nwarps) {
-        const Chunk ch = chunks[c];
-        const JobDesc job = jobs[ch.job];
-        using Bin = typename std::conditional<KIND == RDCT_KIND_RDCT, unsigned, float>::type;
-        Bin bins[64];
-#pragma unroll
-        for (int p = 0; p < 64; ++p) bins[p] = 0;
-        for (int it = ch.item0; it < ch.item0 + ch.nitems; ++it) {
-            const int by = it / job.segs;
-            const int bx = (it - by * job.segs) * 32 + lane;
-            if (bx < job.nbw) {
-                uint32_t w[16];
-                load_block(job.src + (int64_t)by * 8 * job.src_pitch + (int64_t)bx * 8, job.src_pitch, job.align,
-                           w);
-                if constexpr (KIND == RDCT_KIND_RDCT) {
-                    int Y[8][8];
-                    forward_c0(w, Y);
-#pragma unroll
-                    for (int p = 0; p < 64; ++p) bins[p] += (unsigned)(Y[p >> 3][p & 7] * Y[p >> 3][p & 7]);
-                } else {
-                    float Y[8][8], A[8][8];
-                    forward_dct(w, Y, A, C);
-#pragma unroll
-                    for (int p = 0; p < 64; ++p) bins[p] = __fmaf_rn(Y[p >> 3][p & 7], Y[p >> 3][p & 7], bins[p]);
-                }
-            }
-        }
-        double *dst = out + (int64_t)ch.job * 64;
-#pragma unroll
-        for (int p = 0; p < 64; ++p) {
-            const int k = zz_rank(p >> 3, p & 7);
-            if constexpr (KIND == RDCT_KIND_RDCT) {
-                unsigned long long v = (unsigned long long)bins[p] * (unsigned)weight(p >> 3, p & 7);
-                v = warp_sum_u64(v);
-                if (lane == 0 && v) atomicAdd(reinterpret_cast<unsigned long long *>(dst) + k, v);
-            } else {
-                const float v = warp_sum_f32(bins[p]);
-                if (lane == 0 && v != 0.0f) atomicAdd(dst + k, (double)v);
-            }
-        }
-    }
-}
-
 // In place: 64 zigzag bins per plane -> SSE(r) = sum of bins k >= r, r = 1..64.
+// One warp per plane: lane l holds bins 2l and 2l+1; a suffix scan over the
+// warp gives every tail sum.
 __global__ void sweep_finalize_kernel(double *out, int32_t nplanes, int kind) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nplanes) return;
-    double *o = out + (int64_t)i * 64;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= nplanes) return;
+    double *o = out + (int64_t)warp * 64;
     if (kind == RDCT_KIND_RDCT) {
-        unsigned long long *u = reinterpret_cast<unsigned long long *>(o);
-        unsigned long long bins[64];
-        for (int k = 0; k < 64; ++k) bins[k] = u[k];
-        unsigned long long tail = 0;
-        for (int r = 64; r >= 1; --r) {
-            o[r - 1] = (double)tail / 576.0;  // keeps ranks < r, drops ranks >= r
-            tail += bins[r - 1];
+        const unsigned long long *u = reinterpret_cast<const unsigned long long *>(o);
+        const unsigned long long b0 = u[2 * lane], b1 = u[2 * lane + 1];
+        unsigned long long t = b0 + b1;  // suffix sum over lanes >= lane
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long v = __shfl_down_sync(0xffffffffu, t, d);
+            if (lane + d < 32) t += v;
         }
+        __syncwarp();
+        // SSE(r) keeps ranks < r: r = 2l+1 drops bins >= 2l+1, r = 2l+2 drops bins >= 2l+2
+        o[2 * lane] = (double)(t - b0) / 576.0;
+        o[2 * lane + 1] = (double)(t - b0 - b1) / 576.0;
     } else {
-        double bins[64];
-        for (int k = 0; k < 64; ++k) bins[k] = o[k];
-        double tail = 0.0;
-        for (int r = 64; r >= 1; --r) {
-            o[r - 1] = tail;
-            tail += bins[r - 1];
+        const double b0 = o[2 * lane], b1 = o[2 * lane + 1];
+        double t = b0 + b1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double v = __shfl_down_sync(0xffffffffu, t, d);
+            if (lane + d < 32) t += v;
         }
+        __syncwarp();
+        // tails summed from the small end (lanes >= lane), so small bins are not lost
+        o[2 * lane] = t - b0;
+        o[2 * lane + 1] = t - b0 - b1;
     }
 }
 
@@ -359,20 +317,12 @@ cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchun
                          int32_t nplanes, cudaStream_t s) {
     (void)nplanes;
     if (nchunks <= 0) return cudaSuccess;
-    const int warps = 4;
-    int64_t g = (nchunks + warps - 1) / warps;
-    const int64_t cap = (int64_t)sm_count() * 8;
-    if (g > cap) g = cap;
-    if (kind == RDCT_KIND_RDCT)
-        sweep_kernel<RDCT_KIND_RDCT><<<(int)g, warps * 32, 0, s>>>(jobs, chunks, nchunks, out, DctConsts{});
-    else
-        sweep_kernel<RDCT_KIND_DCT><<<(int)g, warps * 32, 0, s>>>(jobs, chunks, nchunks, out, make_dct_consts());
-    return cudaGetLastError();
+    return launch_sweep2(jobs, chunks, nchunks, kind, out, s);
 }
 
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s) {
     if (nplanes <= 0) return cudaSuccess;
-    sweep_finalize_kernel<<<(nplanes + 127) / 128, 128, 0, s>>>(out, nplanes, kind);
+    sweep_finalize_kernel<<<(nplanes + 3) / 4, 128, 0, s>>>(out, nplanes, kind);
     return cudaGetLastError();
 }
 

@@ -7,12 +7,12 @@
 // or synchronise the device, or a plug-in whose host process forbids device
 // allocation outright.  rdct_sweep builds per-call descriptor tables in a
 // stream-ordered allocation; this variant keeps them in one fixed device array
-// that is part of the library image instead, builds them on the device, and
-// otherwise runs the same kernels.  Nothing is allocated, on the device or on
+// that is part of the library image instead; both build them on the device
+// from plane descriptors passed as kernel parameters and run the same kernels.  Nothing is allocated, on the device or on
 // the host, on the success path.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (kNoAllocScratchBytes, about 720 KiB) until the process
+// library holds it (kNoAllocScratchBytes, 672 KiB) until the process
 // exits.  In host code its name is only a host-side stand-in for the device
 // variable, not a device address, so its device address is looked up with
 // cudaGetSymbolAddress, once per device, with that device current, the first
@@ -31,15 +31,13 @@ namespace {
 
 constexpr int32_t kNoAllocMaxPlanes = 2048;
 constexpr int32_t kNoAllocMaxChunks = 32768;
-constexpr int32_t kNoAllocStrips = 16;  // strips per chunk, as in rdct_sweep
 
 constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
-constexpr size_t kPlanesOff = 0;
-constexpr size_t kJobsOff = align256(kPlanesOff + sizeof(rdct_plane) * kNoAllocMaxPlanes);
+constexpr size_t kJobsOff = 0;
 constexpr size_t kChunksOff = align256(kJobsOff + sizeof(JobDesc) * kNoAllocMaxPlanes);
 constexpr size_t kNoAllocScratchBytes = align256(kChunksOff + sizeof(Chunk) * kNoAllocMaxChunks);
 
-// The scratch: planes as passed in, then the job and chunk tables.
+// The scratch: the job table, then the chunk table.
 static __device__ __align__(256) unsigned char g_sweep_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -63,48 +61,6 @@ rdct_status scratch_address(unsigned char **out) {
     return RDCT_OK;
 }
 
-__device__ int align_class(const void *p, int64_t pitch) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-    if ((a % 16) == 0 && (pitch % 16) == 0) return 16;
-    if ((a % 8) == 0 && (pitch % 8) == 0) return 8;
-    return 1;
-}
-
-// Builds the job table (one descriptor per plane, one block per thread,
-// strips of 32 blocks) and the chunk table (runs of <= 16 strips) from the
-// planes copied into the scratch.  One CTA; n <= kNoAllocMaxPlanes.
-__global__ void build_sweep_tables_kernel(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks) {
-    __shared__ int32_t s_off[kNoAllocMaxPlanes + 1];
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const rdct_plane pl = planes[i];
-        JobDesc j{};
-        j.src = pl.ptr;
-        j.src_pitch = pl.pitch;
-        j.nbw = pl.w / 8;
-        j.nbh = pl.h / 8;
-        j.r = 64;
-        j.image = i;
-        j.segs = (j.nbw + 31) / 32;
-        j.align = align_class(pl.ptr, pl.pitch);
-        j.dalign = 16;
-        jobs[i] = j;
-        const int32_t items = j.nbh * j.segs;
-        s_off[i + 1] = (items + kNoAllocStrips - 1) / kNoAllocStrips;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_off[0] = 0;
-        for (int32_t i = 0; i < n; ++i) s_off[i + 1] += s_off[i];
-    }
-    __syncthreads();
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const int32_t items = jobs[i].nbh * jobs[i].segs;
-        int32_t c = s_off[i];
-        for (int32_t it = 0; it < items; it += kNoAllocStrips, ++c)
-            chunks[c] = Chunk{i, it, items - it < kNoAllocStrips ? items - it : kNoAllocStrips, 0};
-    }
-}
-
 }  // namespace
 }  // namespace rdct
 
@@ -122,24 +78,21 @@ extern "C" rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, r
     for (int32_t i = 0; i < n; ++i) {
         rdct_status st = validate_plane(&planes[i], "rdct_sweep_noalloc");
         if (st) return st;
-        const int64_t items = (int64_t)(planes[i].h / 8) * ((planes[i].w / 8 + 31) / 32);
-        nchunks += (items + kNoAllocStrips - 1) / kNoAllocStrips;
+        nchunks += sweep_chunk_count(planes[i]);
     }
     if (nchunks > kNoAllocMaxChunks)
-        return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: the planes need more than 32768 chunks of 16 "
-                                             "strips (about 1.07 Gpixel in one call); split the call or use rdct_sweep");
+        return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: the planes need more than 32768 chunks of 512 "
+                                             "blocks (about 1.07 Gpixel in one call); split the call or use rdct_sweep");
     if (n == 0) return RDCT_OK;
     unsigned char *base = nullptr;
     rdct_status st = scratch_address(&base);
     if (st) return st;
-    rdct_plane *d_planes = reinterpret_cast<rdct_plane *>(base + kPlanesOff);
     JobDesc *d_jobs = reinterpret_cast<JobDesc *>(base + kJobsOff);
     Chunk *d_chunks = reinterpret_cast<Chunk *>(base + kChunksOff);
     cudaStream_t s = (cudaStream_t)stream;
-    // the tables are rewritten in full by every call; only the output bins must start at zero
-    RDCT_CUDA_TRY(cudaMemcpyAsync(d_planes, planes, sizeof(rdct_plane) * (size_t)n, cudaMemcpyHostToDevice, s));
-    build_sweep_tables_kernel<<<1, 256, 0, s>>>(d_planes, n, d_jobs, d_chunks);
-    RDCT_CUDA_TRY(cudaGetLastError());
+    // the tables are rewritten in full by every call (from plane descriptors
+    // passed as kernel parameters); only the output bins must start at zero
+    RDCT_CUDA_TRY(build_sweep_tables(planes, n, d_jobs, d_chunks, s));
     RDCT_CUDA_TRY(cudaMemsetAsync(sse_by_r, 0, (size_t)n * 64 * sizeof(double), s));
     RDCT_CUDA_TRY(launch_sweep(d_jobs, d_chunks, (int32_t)nchunks, (int)kind, sse_by_r, n, s));
     RDCT_CUDA_TRY(launch_sweep_finalize(sse_by_r, n, (int)kind, s));

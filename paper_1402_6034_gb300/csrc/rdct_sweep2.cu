@@ -1,0 +1,102 @@
+// Launches of the one-pass r sweep (see rdct_sweep2.cuh) and the on-device
+// construction of its job and chunk tables.
+#include <algorithm>
+
+#include "rdct_sweep2.cuh"
+
+namespace rdct {
+
+cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
+                          cudaStream_t s) {
+    if (nchunks <= 0) return cudaSuccess;
+    Fused2Args a{};
+    a.jobs = jobs;
+    a.chunks = chunks;
+    a.nchunks = nchunks;
+    if (kind == RDCT_KIND_RDCT)
+        launch_persistent(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, s, a, out, DctConsts{});
+    else
+        launch_persistent(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, s, a, out, make_dct_consts());
+    return cudaGetLastError();
+}
+
+namespace {
+
+__device__ int align_class(const void *p, int64_t pitch) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    if ((a % 16) == 0 && (pitch % 16) == 0) return 16;
+    if ((a % 8) == 0 && (pitch % 8) == 0) return 8;
+    return 1;
+}
+
+// Up to kSweepBuildBatch planes, passed by value so that building the tables
+// needs no host-to-device copy (and no stream synchronisation).
+struct PlaneBatch {
+    rdct_plane p[kSweepBuildBatch];
+    int32_t first, n, chunk_base;
+};
+
+// One CTA: a job descriptor per plane (strips of kFusedVRows block rows by 32
+// blocks) and the chunks (runs of at most kSweepChunkStrips strips) of this
+// batch, starting at chunk index chunk_base.
+__global__ void __launch_bounds__(1024) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks) {
+    __shared__ int32_t s_cnt[kSweepBuildBatch + 1];
+    const int i = threadIdx.x;
+    int32_t items = 0;
+    if (i < b.n) {
+        const rdct_plane pl = b.p[i];
+        JobDesc j{};
+        j.src = pl.ptr;
+        j.src_pitch = pl.pitch;
+        j.nbw = pl.w / 8;
+        j.nbh = pl.h / 8;
+        j.r = 64;
+        j.image = b.first + i;
+        j.segs = (j.nbw + 31) / 32;
+        j.align = align_class(pl.ptr, pl.pitch);
+        j.dalign = 16;
+        jobs[b.first + i] = j;
+        items = strips_of(j, kFusedVRows);
+    }
+    s_cnt[i + 1] = (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
+    __syncthreads();
+    // inclusive scan of the chunk counts (Hillis-Steele over the CTA)
+    for (int off = 1; off < kSweepBuildBatch; off <<= 1) {
+        const int32_t v = (i + 1 - off >= 1) ? s_cnt[i + 1 - off] : 0;
+        __syncthreads();
+        s_cnt[i + 1] += v;
+        __syncthreads();
+    }
+    if (i < b.n) {
+        int32_t c = b.chunk_base + (i == 0 ? 0 : s_cnt[i]);
+        for (int32_t it = 0; it < items; it += kSweepChunkStrips, ++c)
+            chunks[c] = Chunk{b.first + i, it, items - it < kSweepChunkStrips ? items - it : kSweepChunkStrips, 0};
+    }
+}
+
+}  // namespace
+
+int64_t sweep_chunk_count(const rdct_plane &p) {
+    const int64_t items = (int64_t)((p.h / 8 + kFusedVRows - 1) / kFusedVRows) * ((p.w / 8 + 31) / 32);
+    return (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
+}
+
+cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, cudaStream_t s) {
+    int32_t base = 0;
+    for (int32_t first = 0; first < n; first += kSweepBuildBatch) {
+        PlaneBatch b;
+        b.first = first;
+        b.n = std::min(kSweepBuildBatch, n - first);
+        b.chunk_base = base;
+        for (int32_t i = 0; i < b.n; ++i) {
+            b.p[i] = planes[first + i];
+            base += (int32_t)sweep_chunk_count(planes[first + i]);
+        }
+        build_sweep_tables_kernel<<<1, kSweepBuildBatch, 0, s>>>(b, jobs, chunks);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace rdct

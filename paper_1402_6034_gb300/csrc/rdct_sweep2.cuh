@@ -1,0 +1,153 @@
+// rdct_sweep2.cuh -- the r sweep of Sec. 3 in one pass per plane.
+//
+// The transforms are orthogonal (Sec. 2), so the squared error of the
+// reconstruction that keeps the first r zigzag coefficients is the energy of
+// the dropped orthonormal coefficients (Parseval).  One pass per plane
+// therefore gives the error for every r: each thread transforms its blocks,
+// adds every coefficient's energy into 64 per-position bins held in
+// registers, and once per chunk the warp reduces the bins and adds them to the
+// plane's 64 zigzag-ordered bins; suffix sums then give SSE(r), r = 1..64.
+//
+// RDCT: Y = C0 A C0^T exactly (dp4a row pass on packed pixels, int32 column
+// butterfly); the orthonormal energy of Y_ij is W_ij Y_ij^2 / 576, so the bins
+// hold integer Y^2 sums (exact) and the weights are applied at the flush.
+// DCT: C A C^T in FP32 (even/odd split, FMAs with the cos constants), FP32
+// bins, FP64 plane bins.
+// Staging, strip cursors and chunking are those of the fused kernel.
+#pragma once
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+
+// Strips per sweep chunk (kSweepChunkStrips): a thread adds at most
+// 2 * 8 = 16 blocks into a 32-bit bin before the flush, and one block adds at
+// most 16320^2 < 2^28 to a bin, so 16 blocks fit.
+static_assert(kSweepChunkStrips * kFusedVRows * 16320ull * 16320ull < (1ull << 32), "sweep bins overflow");
+
+__device__ __forceinline__ void sweep_rdct_block(const uint2 (&w)[8], unsigned (&bins)[64]) {
+    int R[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            R[i][k] = dp4a_us(w[i].x, c0_row_word(k, 0), dp4a_us(w[i].y, c0_row_word(k, 1), 0));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int c[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
+        c0_forward(c, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bins[i * 8 + j] += (unsigned)(o[i] * o[i]);
+    }
+}
+
+__device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
+    float R[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float x[8];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            x[n] = (float)byte_of(w[i].x, n);
+            x[n + 4] = (float)byte_of(w[i].y, n);
+        }
+        dct_fwd8(x, R[i], C);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float c[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
+        dct_fwd8(c, o, C);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bins[i * 8 + j] = __fmaf_rn(o[i], o[i], bins[i * 8 + j]);
+    }
+}
+
+// Sum of a 32-bit value over the warp in 64 bits (two 16-bit halves, each
+// summed with one warp reduction).
+__device__ __forceinline__ unsigned long long warp_sum_u32_wide(unsigned v) {
+    const unsigned lo = __reduce_add_sync(0xffffffffu, v & 0xFFFFu);
+    const unsigned hi = __reduce_add_sync(0xffffffffu, v >> 16);
+    return ((unsigned long long)hi << 16) + lo;
+}
+
+template <int KIND>
+__device__ __forceinline__ void sweep_flush(double *plane_bins, unsigned (&ub)[64], float (&fb)[64], int lane) {
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+        const int k = zz_rank(p >> 3, p & 7);
+        if constexpr (KIND == RDCT_KIND_RDCT) {
+            const unsigned long long s = warp_sum_u32_wide(ub[p]) * (unsigned)weight(p >> 3, p & 7);
+            if (lane == (p & 31) && s) atomicAdd(reinterpret_cast<unsigned long long *>(plane_bins) + k, s);
+            ub[p] = 0u;
+        } else {
+            const float s = warp_sum_f32(fb[p]);
+            if (lane == (p & 31) && s != 0.0f) atomicAdd(plane_bins + k, (double)s);
+            fb[p] = 0.0f;
+        }
+    }
+}
+
+// Persistent sweep kernel over a chunk table (job = plane; out = [planes][64]
+// zigzag-ordered bins: uint64 576-scaled energies for RDCT, double for DCT).
+template <int KIND>
+__global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, double *out, const DctConsts C) {
+    constexpr int THREADS = 128;
+    __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    unsigned ub[64];
+    float fb[64];
+#pragma unroll
+    for (int p = 0; p < 64; ++p) {
+        ub[p] = 0u;
+        fb[p] = 0.0f;
+    }
+    Cursor fc{gw, 0, 0, 0, 0, 0};
+    cursor_load<false>(a, fc);
+    Cursor cc = fc;
+#pragma unroll
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (fc.c < a.nchunks) {
+            fetch_strip<THREADS>(a.jobs[fc.job], fc.by, fc.seg, lane, ring, s);
+            cursor_next<false>(a, fc, nwarps);
+        } else {
+            cp_async_commit();
+        }
+    }
+    int stage = 0;
+    while (cc.c < a.nchunks) {
+        cp_async_wait<kStages - 2>();
+        const JobDesc &job = a.jobs[cc.job];
+        const int bx = cc.seg * 32 + lane;
+        const int nblk = bx < job.nbw ? (job.nbh - cc.by >= kVRows ? kVRows : job.nbh - cc.by) : 0;
+        const int refill = stage == 0 ? kStages - 1 : stage - 1;
+        if (fc.c < a.nchunks) {
+            fetch_strip<THREADS>(a.jobs[fc.job], fc.by, fc.seg, lane, ring, refill);
+            cursor_next<false>(a, fc, nwarps);
+        } else {
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int v = 0; v < kVRows; ++v) {
+            if (v < nblk) {
+                uint2 w[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
+                if constexpr (KIND == RDCT_KIND_RDCT) sweep_rdct_block(w, ub);
+                else sweep_dct_block(w, fb, C);
+            }
+        }
+        stage = stage + 1 == kStages ? 0 : stage + 1;
+        const int plane = cc.job;
+        const int cprev = cc.c;
+        cursor_next<false>(a, cc, nwarps);
+        if (cc.c != cprev) sweep_flush<KIND>(out + (int64_t)plane * 64, ub, fb, lane);
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace rdct

@@ -1,0 +1,117 @@
+"""Parity at full size, in the launch configuration bench.py times.
+
+The 600-frame 3840x2160 YUV 4:2:0 clip at r = 16 and the 4096-image uneven
+batch are run exactly as bench.py runs them (one graph launch of a batch
+plan).  The oracle then recomputes sampled 8x8 blocks one by one (uint8
+output and the block's squared error), and properties that hold at any size
+are checked on everything:
+  * per-frame SSE of the fused path == sum over its planes of SSE(r) from the
+    r sweep (an independent kernel: all 64 coefficient energies, Parseval,
+    suffix sums), exactly;
+  * whole sampled frames / images (every plane) match the oracle's uint8
+    reconstruction and squared error.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1402_6034_gb300 import rdct
+from tests.gpu_helpers import assert_u8_close, cuda_or_skip
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    d = cuda_or_skip()
+    rdct.load()
+    return d
+
+
+def _sample_blocks(planes, outs, frames, r, rng, n_samples):
+    """Compare n_samples random 8x8 blocks against the oracle (uint8 and squared error)."""
+    for _ in range(n_samples):
+        f = int(rng.integers(0, frames))
+        k = int(rng.integers(0, len(planes)))
+        p = planes[k][f]
+        h, w = p.shape
+        by, bx = int(rng.integers(0, h // 8)), int(rng.integers(0, w // 8))
+        blk = p[by * 8:by * 8 + 8, bx * 8:bx * 8 + 8].cpu().numpy()
+        got = outs[k][f][by * 8:by * 8 + 8, bx * 8:bx * 8 + 8].cpu().numpy()
+        xo, uo, _, _ = orc.fused(np.ascontiguousarray(blk), r)
+        assert_u8_close(got, uo, xo, tie_window=1e-6)
+
+
+def test_video_600_frames_4k_r16(dev):
+    import bench
+    wl = bench.VideoWorkload(600, 16, dev)
+    stream = torch.cuda.current_stream()
+    wl.step(stream)
+    wl.step(stream)  # graph replay, as in the timed loop
+    torch.cuda.synchronize()
+    sse = wl.sse.clone()
+    # independent kernel: the sweep's SSE(16) summed over the three planes of each frame
+    sw = torch.zeros(600, dtype=torch.float64, device=dev)
+    for p in wl.planes:
+        sw += rdct.sweep(p, rdct.KIND_RDCT)[:, 15]
+    torch.cuda.synchronize()
+    assert torch.allclose(sse, sw, rtol=1e-12, atol=1e-9), (sse[:4], sw[:4])
+    rng = np.random.Generator(np.random.PCG64(0))
+    _sample_blocks(wl.planes, wl.out, 600, 16, rng, 300)
+    # whole frames against the oracle for a few frames (all planes)
+    for f in (0, 299, 599):
+        tot = 0.0
+        for k, p in enumerate(wl.planes):
+            img = p[f].cpu().numpy()
+            xo, uo, so, _ = orc.fused(img, 16, want_xhat=True, want_u8=True, nthreads=0)
+            assert_u8_close(wl.out[k][f].cpu().numpy(), uo, xo, tie_window=1e-6)
+            tot += so
+        assert sse[f].item() == pytest.approx(tot, rel=1e-9)
+
+
+def test_uneven_4096_images(dev):
+    from paper_1402_6034_gb300 import synth
+    n = 4096
+    specs = synth.uneven_specs(n, seed=0)
+    pool = synth.field_u8_torch(2048, 2048, 2.0, 0, device=str(dev), planes=4)
+    rng = np.random.Generator(np.random.PCG64(1))
+    total = sum(sp.w * sp.h * sp.planes for sp in specs)
+    src_buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    dst_buf = torch.empty(total, dtype=torch.uint8, device=dev)
+    jobs, off = [], 0
+    for i, sp in enumerate(specs):
+        for p in range(sp.planes):
+            k = int(rng.integers(0, 4))
+            y0, x0 = int(rng.integers(0, 2048 - sp.h + 1)), int(rng.integers(0, 2048 - sp.w + 1))
+            src = src_buf[off:off + sp.w * sp.h].view(sp.h, sp.w)
+            src.copy_(pool[k, y0:y0 + sp.h, x0:x0 + sp.w])
+            jobs.append(rdct.BatchJob(src, dst_buf[off:off + sp.w * sp.h].view(sp.h, sp.w), sp.r, i))
+            off += sp.w * sp.h
+    plan = rdct.BatchPlan(jobs, n)
+    sse = torch.empty(n, dtype=torch.float64, device=dev)
+    plan.run(sse)
+    torch.cuda.synchronize()
+    # independent kernel per plane: the sweep at each plane's r
+    sw = torch.zeros(n, dtype=torch.float64, device=dev)
+    by_r = {}
+    for j in jobs:
+        by_r.setdefault(j.r, []).append(j)
+    for r, js in by_r.items():
+        out = rdct.sweep([j.src for j in js], rdct.KIND_RDCT)[:, r - 1]
+        idx = torch.tensor([j.image for j in js], device=dev)
+        sw.index_add_(0, idx, out)
+    torch.cuda.synchronize()
+    assert torch.allclose(sse, sw, rtol=1e-12, atol=1e-9)
+    # sampled whole images against the oracle
+    srng = np.random.Generator(np.random.PCG64(2))
+    for i in srng.choice(n, 12, replace=False):
+        tot = 0.0
+        for j in jobs:
+            if j.image != i:
+                continue
+            img = j.src.cpu().numpy()
+            xo, uo, so, _ = orc.fused(img, j.r)
+            assert_u8_close(j.dst.cpu().numpy(), uo, xo, tie_window=1e-6)
+            tot += so
+        assert sse[int(i)].item() == pytest.approx(tot, rel=1e-9)
