@@ -35,8 +35,6 @@ struct rdct_plan {
     // graph cache: one executable per (sse pointer)
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t branch[kBatchGroups] = {nullptr};  // capture-time forks: groups run as parallel graph branches
-    cudaEvent_t fork = nullptr, join[kBatchGroups] = {nullptr};
     cudaGraphExec_t exec = nullptr;
     double *exec_sse = nullptr;
 };
@@ -100,26 +98,17 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     for (int g = 0; g < kBatchGroups; ++g) p->group_begin[g + 1] += p->group_begin[g];
 }
 
-// memset -> one persistent kernel per non-empty group (forked onto their own
-// streams when there are several, so they become parallel graph branches and
-// fill the GPU together) -> join -> in-place 576*SSE to SSE.
+// memset -> one persistent kernel per non-empty group, in stream order (the
+// groups overlap only at their tails; running them as parallel graph branches
+// measured slower) -> in-place 576*SSE to SSE.
 cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
-    int groups = 0;
-    for (int g = 0; g < kBatchGroups; ++g) groups += p->group_begin[g + 1] > p->group_begin[g];
-    const bool fork = groups > 1;
-    if (fork && e == cudaSuccess) e = cudaEventRecord(p->fork, s);
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
         if (n == 0) continue;
-        cudaStream_t gs = fork ? p->branch[g] : s;
-        if (fork) e = cudaStreamWaitEvent(gs, p->fork, 0);
-        if (e == cudaSuccess)
-            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm, p->tune.warps_per_cta,
-                                   p->tune.blocks_per_thread, gs);
-        if (fork && e == cudaSuccess) e = cudaEventRecord(p->join[g], gs);
-        if (fork && e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join[g], 0);
+        e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm, p->tune.warps_per_cta,
+                               p->tune.blocks_per_thread, s);
     }
     if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
     return e;
@@ -185,12 +174,7 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     if (jb) e = cudaMemcpy(p->d_jobs, p->jobs.data(), jb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && cb) e = cudaMemcpy(p->d_chunks, p->chunks.data(), cb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
-    for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
-        if (p->group_begin[g + 1] == p->group_begin[g]) continue;
-        e = cudaStreamCreateWithFlags(&p->branch[g], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[g], cudaEventDisableTiming);
-    }
+
     if (e != cudaSuccess) {
         rdct_batch_plan_destroy(p);
         return cuda_error(e, "rdct_batch_plan_create");
@@ -252,11 +236,6 @@ rdct_status rdct_batch_plan_destroy(rdct_plan *p) {
         cudaStreamSynchronize(p->cap_stream);
         cudaStreamDestroy(p->cap_stream);
     }
-    for (int g = 0; g < kBatchGroups; ++g) {
-        if (p->branch[g]) cudaStreamDestroy(p->branch[g]);
-        if (p->join[g]) cudaEventDestroy(p->join[g]);
-    }
-    if (p->fork) cudaEventDestroy(p->fork);
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_chunks) cudaFree(p->d_chunks);
     delete p;

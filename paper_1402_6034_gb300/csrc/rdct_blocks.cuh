@@ -385,6 +385,26 @@ inline void launch_persistent(K kernel, int64_t units, int ctas_per_sm, int warp
     kernel<<<(int)(g < 1 ? 1 : g), threads, 0, s>>>(args...);
 }
 
+// Persistent launch of a kernel that stages rows through a shared-memory
+// ring: at most max_ctas CTAs per SM, and the shared-memory carve-out set to
+// the smallest size that holds them, so the rest of the SM's 256 KB stays L1
+// (the copies into the ring are cached in L1; a larger carve-out measurably
+// slows them down).
+template <typename K, typename... Args>
+inline void launch_staged(K kernel, int64_t units, int ctas_per_sm, int warps, int max_ctas, int smem_per_cta,
+                          cudaStream_t s, Args... args) {
+    const int threads = warps * 32;
+    int per_sm = resident_ctas(kernel, threads);
+    if (per_sm > max_ctas) per_sm = max_ctas;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    const int pct = (int)((100LL * per_sm * (smem_per_cta + 1024) + 228 * 1024 - 1) / (228 * 1024));
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+    int64_t g = (int64_t)sm_count() * per_sm;
+    const int64_t need = (units + warps - 1) / warps;
+    if (g > need) g = need;
+    kernel<<<(int)(g < 1 ? 1 : g), threads, 0, s>>>(args...);
+}
+
 // Single-plane fused launch for one output mode and transform kind; the
 // anti-diagonal class d selects the specialised kernel.
 template <int OUT, int KIND>

@@ -2,7 +2,7 @@
 // transform, zonal truncation with the S scaling of Sec. 2, inverse, squared
 // error) shaped for sm_103a issue rates.
 //
-// Per 8x8 block, one thread:
+// Per 8x8 block (a thread owns two vertically adjacent blocks):
 //   * rows of pixels arrive through a per-thread cp.async ring in shared
 //     memory (three stages in flight, no block barriers: each thread only
 //     reads what it copied itself);
@@ -14,8 +14,8 @@
 //   * compression: kept coefficients become Z = W Y with W = 576 d_i^2 d_j^2,
 //     converted exactly to FP32 in units of 2^-149 (subnormal range);
 //   * inverse: C0^T butterflies in FP32, exact because every value is an
-//     integer multiple of 2^-149 below 2^24 units; the row pass runs on
-//     packed pairs of rows (f32x2);
+//     integer multiple of 2^-149 below 2^24 units; the column pass is scalar,
+//     the row pass runs on f32x2 pairs of rows;
 //   * output: one f32x2 multiply by 1/576 leaves round(Xhat) in the bit
 //     pattern of each float (negative values carry the sign bit), and
 //     cvt.pack.sat clamps to [0, 255] and packs four pixels per two
@@ -61,6 +61,7 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
     return d;
 }
+
 
 // ------------------------------------------------------------ int helpers
 
@@ -182,9 +183,11 @@ __device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], 
 
 // ------------------------------------------------------------------ kernel
 
-// Launch shape per anti-diagonal class: 128 registers (4 CTAs of 128 threads
-// per SM) up to r = 45, 168 above.  Measured: more registers for more
-// independent work per thread beat more resident warps.
+// Launch shape per anti-diagonal class: 128 registers up to r = 45, 168
+// above, and at most kFused2MaxCtas CTAs of 128 threads per SM (see
+// launch_staged).  Measured: more registers for independent work per thread
+// beat more resident warps, and shared memory beyond four rings squeezes the
+// L1 the copies go through.
 template <int D>
 struct Fused2Shape {
     static constexpr int threads = 128;
@@ -192,6 +195,8 @@ struct Fused2Shape {
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
+constexpr int kFused2MaxCtas = 4;    // CTAs per SM (measured best; leaves L1 for the copies)
+constexpr int kFused2Smem = kStages * 8 * kVRows * 128 * 8;  // ring bytes per 128-thread CTA
 
 __device__ __forceinline__ void cp_async8(uint32_t smem_addr, const void *gptr) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr), "l"(gptr) : "memory");
@@ -202,14 +207,13 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Work description shared by the single-plane and batch launches.  A strip
-// (work item) is kVRows block rows by 32 blocks; item t of a plane is
-// strip-row t / segs, segment t % segs.
+// Work description shared by the single-plane and batch launches.  Items are
+// runs of 32 consecutive column pairs of a plane (see fused_items_of).
 struct Fused2Args {
     const JobDesc *jobs;       // batch: device job table; single: unused
     const Chunk *chunks;       // batch: device chunk table; single: unused
     int32_t nchunks;
-    int32_t chunk_items;       // single: strips per virtual chunk
+    int32_t chunk_items;       // single: items per virtual chunk
     unsigned long long *acc;   // batch: per-image 576*SSE; single: one slot
     JobDesc single;            // single-plane job (by value)
 };
@@ -217,7 +221,7 @@ struct Fused2Args {
 template <bool SINGLE>
 __device__ __forceinline__ Chunk get_chunk(const Fused2Args &a, int c) {
     if constexpr (SINGLE) {
-        const int total = ((a.single.nbh + kVRows - 1) / kVRows) * a.single.segs;
+        const int total = fused_items_of(a.single);
         const int it0 = c * a.chunk_items;
         const int n = total - it0 < a.chunk_items ? total - it0 : a.chunk_items;
         return Chunk{0, it0, n, diag_class(a.single.r)};
@@ -231,43 +235,46 @@ __device__ __forceinline__ const JobDesc &get_job(const Fused2Args &a, int j) {
     else return a.jobs[j];
 }
 
-// Walks the strips of one warp: chunks c = warp, warp + nwarps, ...; inside a
-// chunk the strips advance segment by segment without divisions.
+// Walks the items of one warp: chunks c = warp, warp + nwarps, ...; each lane
+// tracks its own column pair (row pair rp, block column bx), advanced by 32
+// per item without divisions.
 struct Cursor {
-    int c, by, seg, left, job, diag;
+    int c, left, job, diag, rp, bx;
 };
 template <bool SINGLE>
-__device__ __forceinline__ void cursor_load(const Fused2Args &a, Cursor &cu) {
+__device__ __forceinline__ void cursor_load(const Fused2Args &a, Cursor &cu, int lane) {
     if (cu.c < a.nchunks) {
         const Chunk ch = get_chunk<SINGLE>(a, cu.c);
-        const int segs = get_job<SINGLE>(a, ch.job).segs;
-        const int g = ch.item0 / segs;
-        cu.by = g * kVRows;
-        cu.seg = ch.item0 - g * segs;
+        const int nbw = get_job<SINGLE>(a, ch.job).nbw;
+        const int L = ch.item0 * 32 + lane;
+        cu.rp = L / nbw;
+        cu.bx = L - cu.rp * nbw;
         cu.left = ch.nitems;
         cu.job = ch.job;
         cu.diag = ch.diag;
     }
 }
 template <bool SINGLE>
-__device__ __forceinline__ void cursor_next(const Fused2Args &a, Cursor &cu, int nwarps) {
+__device__ __forceinline__ void cursor_next(const Fused2Args &a, Cursor &cu, int nwarps, int lane) {
     if (--cu.left > 0) {
-        if (++cu.seg == get_job<SINGLE>(a, cu.job).segs) {
-            cu.seg = 0;
-            cu.by += kVRows;
+        const int nbw = get_job<SINGLE>(a, cu.job).nbw;
+        cu.bx += 32;
+        while (cu.bx >= nbw) {
+            cu.bx -= nbw;
+            ++cu.rp;
         }
     } else {
         cu.c += nwarps;
-        cursor_load<SINGLE>(a, cu);
+        cursor_load<SINGLE>(a, cu, lane);
     }
 }
 
-// Copy this lane's blocks of a strip into ring stage `st` (rows of block v at
-// ring rows 8v .. 8v+7).
+// Copy this lane's blocks (rows of block v at ring rows 8v .. 8v+7) into ring
+// stage `st`.
 template <int THREADS>
-__device__ __forceinline__ void fetch_strip(const JobDesc &job, int by, int seg, int lane, uint2 *ring, int st) {
-    const int bx = seg * 32 + lane;
-    if (bx < job.nbw) {
+__device__ __forceinline__ void fetch_strip(const JobDesc &job, int rp, int bx, uint2 *ring, int st) {
+    const int by = rp * kVRows;
+    if (by < job.nbh) {
         const int64_t pitch = job.src_pitch;
         const uint8_t *src = job.src + (int64_t)by * 8 * pitch + (int64_t)bx * 8;
         uint2 *dst = ring + st * 8 * kVRows * THREADS + threadIdx.x;
@@ -309,13 +316,13 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 
     Cursor fc{gw, 0, 0, 0, 0, 0};
-    cursor_load<SINGLE>(a, fc);
+    cursor_load<SINGLE>(a, fc, lane);
     Cursor cc = fc;
 #pragma unroll
     for (int s = 0; s < kStages - 1; ++s) {
         if (fc.c < a.nchunks) {
-            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.by, fc.seg, lane, ring, s);
-            cursor_next<SINGLE>(a, fc, nwarps);
+            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.rp, fc.bx, ring, s);
+            cursor_next<SINGLE>(a, fc, nwarps, lane);
         } else {
             cp_async_commit();
         }
@@ -325,21 +332,18 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
     while (cc.c < a.nchunks) {
         cp_async_wait<kStages - 2>();
         const JobDesc &job = get_job<SINGLE>(a, cc.job);
-        const int bx = cc.seg * 32 + lane;
-        const int nblk = bx < job.nbw ? (job.nbh - cc.by >= kVRows ? kVRows : job.nbh - cc.by) : 0;
+        const int by = cc.rp * kVRows;
+        const int nblk = by < job.nbh ? (job.nbh - by >= kVRows ? kVRows : job.nbh - by) : 0;
         const int refill = stage == 0 ? kStages - 1 : stage - 1;
         if (fc.c < a.nchunks) {
-            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.by, fc.seg, lane, ring, refill);
-            cursor_next<SINGLE>(a, fc, nwarps);
+            fetch_strip<THREADS>(get_job<SINGLE>(a, fc.job), fc.rp, fc.bx, ring, refill);
+            cursor_next<SINGLE>(a, fc, nwarps, lane);
         } else {
             cp_async_commit();
         }
-        uint8_t *dst = job.dst ? job.dst + (int64_t)cc.by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
-        const int r = job.r;
-        const int64_t dpitch = job.dst_pitch;
-        const int dalign = job.dalign;
-        // both blocks of the strip (the refill above went to the other stage); unrolled
-        // so that their independent work interleaves
+        uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)cc.bx * 8 : nullptr;
+        // both blocks of the column pair, one after the other in the code but
+        // unrolled so that their independent work interleaves
 #pragma unroll
         for (int v = 0; v < kVRows; ++v) {
             if (v < nblk) {
@@ -348,15 +352,15 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
                 for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
                 static_for<DLO, DHI + 1>([&](auto dc) {
                     constexpr int d = decltype(dc)::value;
-                    if (cc.diag == d) s576 += fused2_block<d>(w, r, dst, dpitch, dalign);
+                    if (cc.diag == d) s576 += fused2_block<d>(w, job.r, dst, job.dst_pitch, job.dalign);
                 });
             }
-            if (dst) dst += 8 * dpitch;
+            if (dst) dst += 8 * job.dst_pitch;
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
         const int img = job.image;
         const int cprev = cc.c;
-        cursor_next<SINGLE>(a, cc, nwarps);
+        cursor_next<SINGLE>(a, cc, nwarps, lane);
         if (cc.c != cprev) {  // end of a chunk: one atomic per warp
             const unsigned long long t = warp_sum_u64(s576);
             if (lane == 0 && t) atomicAdd(SINGLE ? a.acc : a.acc + img, t);

@@ -24,10 +24,19 @@ struct JobDesc {
     int32_t pad;
 };
 
-// The fused kernel takes strips of kFusedVRows block rows (one thread owns
-// that many vertically adjacent blocks); the scalar kernel strips of one.
+// The fused kernel's work items: a thread owns kFusedVRows vertically adjacent
+// blocks (a "column pair" of one row pair); the row pairs x columns of a plane
+// are numbered row-major and an item is a run of 32 consecutive column pairs
+// (one per lane), which may wrap into the next row pair, so no lane idles at
+// the end of a row.  The scalar kernel's items are one block row by 32 blocks.
 constexpr int kFusedVRows = 2;
-__host__ __device__ inline int32_t strips_of(const JobDesc &j, int vrows) { return ((j.nbh + vrows - 1) / vrows) * j.segs; }
+__host__ __device__ inline int32_t fused_items_of(const JobDesc &j) {
+    const int64_t pairs = (int64_t)((j.nbh + kFusedVRows - 1) / kFusedVRows) * j.nbw;
+    return (int32_t)((pairs + 31) / 32);
+}
+__host__ __device__ inline int32_t strips_of(const JobDesc &j, int vrows) {
+    return vrows == kFusedVRows ? fused_items_of(j) : j.nbh * j.segs;
+}
 
 // A run of consecutive strips of one job handed to one warp.
 struct Chunk {

@@ -14,9 +14,10 @@ cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchu
     a.chunks = chunks;
     a.nchunks = nchunks;
     if (kind == RDCT_KIND_RDCT)
-        launch_persistent(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, s, a, out, DctConsts{});
+        launch_staged(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, s, a, out, DctConsts{});
     else
-        launch_persistent(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, s, a, out, make_dct_consts());
+        launch_staged(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, s, a, out,
+                      make_dct_consts());
     return cudaGetLastError();
 }
 
@@ -36,9 +37,9 @@ struct PlaneBatch {
     int32_t first, n, chunk_base;
 };
 
-// One CTA: a job descriptor per plane (strips of kFusedVRows block rows by 32
-// blocks) and the chunks (runs of at most kSweepChunkStrips strips) of this
-// batch, starting at chunk index chunk_base.
+// One CTA: a job descriptor per plane and the chunks (runs of at most
+// kSweepChunkStrips items of 32 column pairs) of this batch, starting at
+// chunk index chunk_base.
 __global__ void __launch_bounds__(1024) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks) {
     __shared__ int32_t s_cnt[kSweepBuildBatch + 1];
     const int i = threadIdx.x;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(1024) build_sweep_tables_kernel(const PlaneBat
         j.align = align_class(pl.ptr, pl.pitch);
         j.dalign = 16;
         jobs[b.first + i] = j;
-        items = strips_of(j, kFusedVRows);
+        items = fused_items_of(j);
     }
     s_cnt[i + 1] = (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
     __syncthreads();
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(1024) build_sweep_tables_kernel(const PlaneBat
 }  // namespace
 
 int64_t sweep_chunk_count(const rdct_plane &p) {
-    const int64_t items = (int64_t)((p.h / 8 + kFusedVRows - 1) / kFusedVRows) * ((p.w / 8 + 31) / 32);
+    const int64_t pairs = (int64_t)((p.h / 8 + kFusedVRows - 1) / kFusedVRows) * (p.w / 8);
+    const int64_t items = (pairs + 31) / 32;
     return (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
 }
 

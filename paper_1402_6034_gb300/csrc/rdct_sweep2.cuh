@@ -107,13 +107,13 @@ __global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, doub
         fb[p] = 0.0f;
     }
     Cursor fc{gw, 0, 0, 0, 0, 0};
-    cursor_load<false>(a, fc);
+    cursor_load<false>(a, fc, lane);
     Cursor cc = fc;
 #pragma unroll
     for (int s = 0; s < kStages - 1; ++s) {
         if (fc.c < a.nchunks) {
-            fetch_strip<THREADS>(a.jobs[fc.job], fc.by, fc.seg, lane, ring, s);
-            cursor_next<false>(a, fc, nwarps);
+            fetch_strip<THREADS>(a.jobs[fc.job], fc.rp, fc.bx, ring, s);
+            cursor_next<false>(a, fc, nwarps, lane);
         } else {
             cp_async_commit();
         }
@@ -122,12 +122,12 @@ __global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, doub
     while (cc.c < a.nchunks) {
         cp_async_wait<kStages - 2>();
         const JobDesc &job = a.jobs[cc.job];
-        const int bx = cc.seg * 32 + lane;
-        const int nblk = bx < job.nbw ? (job.nbh - cc.by >= kVRows ? kVRows : job.nbh - cc.by) : 0;
+        const int by = cc.rp * kVRows;
+        const int nblk = by < job.nbh ? (job.nbh - by >= kVRows ? kVRows : job.nbh - by) : 0;
         const int refill = stage == 0 ? kStages - 1 : stage - 1;
         if (fc.c < a.nchunks) {
-            fetch_strip<THREADS>(a.jobs[fc.job], fc.by, fc.seg, lane, ring, refill);
-            cursor_next<false>(a, fc, nwarps);
+            fetch_strip<THREADS>(a.jobs[fc.job], fc.rp, fc.bx, ring, refill);
+            cursor_next<false>(a, fc, nwarps, lane);
         } else {
             cp_async_commit();
         }
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, doub
         stage = stage + 1 == kStages ? 0 : stage + 1;
         const int plane = cc.job;
         const int cprev = cc.c;
-        cursor_next<false>(a, cc, nwarps);
+        cursor_next<false>(a, cc, nwarps, lane);
         if (cc.c != cprev) sweep_flush<KIND>(out + (int64_t)plane * 64, ub, fb, lane);
     }
     cp_async_wait<0>();

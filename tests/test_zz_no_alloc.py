@@ -56,7 +56,7 @@ def test_noalloc_rejects_oversized_calls(dev):
     with pytest.raises(rdct.RdctError) as e:
         rdct.sweep_noalloc([small] * 2049, out)
     assert e.value.status == 4
-    # 2048 planes of 272 block rows x 32 blocks need 17 chunks of 16 strips each: 34816 > 32768
+    # 2048 planes of 272 block rows x 32 blocks need 17 chunks each: 34816 > 32768
     tall = torch.zeros((8 * 16 * 17, 8 * 32), dtype=torch.uint8, device=dev)
     out2 = torch.zeros((2048, 64), dtype=torch.float64, device=dev)
     with pytest.raises(rdct.RdctError) as e:
