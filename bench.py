@@ -364,10 +364,21 @@ def bench_sweep(args, dev):
     ps_r = (10 * torch.log10(255.0 ** 2 / (out_r / (512 * 512)))).cpu().numpy()
     ps_d = (10 * torch.log10(255.0 ** 2 / (out_d / (512 * 512)))).cpu().numpy()
     rows = {}
+    n_uqi = 64  # UQI needs the reconstruction itself: a 64-image subset, one fused + one UQI launch each
     for r in (1, 5, 10, 16, 32, 45, 63):
+        q = {}
+        for kind in (rdct.KIND_RDCT, rdct.KIND_DCT):
+            acc = torch.zeros((), dtype=torch.float64, device=dev)
+            for i in range(n_uqi):
+                rec = rdct.fused(imgs[i], r, kind, stream=stream)[0]
+                acc += rdct.uqi(imgs[i], rec, stream=stream)
+            q[kind] = acc.item() / n_uqi
         rows[str(r)] = {"psnr_rdct": float(np.mean(ps_r[:, r - 1])), "psnr_dct": float(np.mean(ps_d[:, r - 1])),
                         "mse_rdct": float(mse_r[r - 1]), "mse_dct": float(mse_d[r - 1]),
-                        "mse_ape_pct": float(100 * abs(mse_r[r - 1] - mse_d[r - 1]) / mse_d[r - 1])}
+                        "mse_ape_pct": float(100 * abs(mse_r[r - 1] - mse_d[r - 1]) / mse_d[r - 1]),
+                        "uqi_rdct": q[rdct.KIND_RDCT], "uqi_dct": q[rdct.KIND_DCT],
+                        "uqi_ape_pct": float(100 * abs(q[rdct.KIND_RDCT] - q[rdct.KIND_DCT]) / q[rdct.KIND_DCT])}
+    uqi_ms = events_time(lambda: rdct.uqi(imgs[0], imgs[1], stream=stream), 20, 3, stream)
     total = n * 512 * 512 * 2  # two transforms per step
     peak, kind = peaks()
     return {"metric": METRIC, "value": total / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -377,7 +388,9 @@ def bench_sweep(args, dev):
                        "samples_per_step": total, "note": "one pass per transform, 1 B/px read"},
             "roofline": {"bound": "hbm", "achieved": total / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": total / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{kind} hbm_gbs"},
-            "gpu_launches": 6 * args.steps, "per_r": rows}
+            "gpu_launches": 6 * args.steps, "per_r": rows,
+            "uqi_kernel": {"image": "512x512 u8", "us": uqi_ms * 1e3,
+                           "windows_per_s": 505 * 505 / (uqi_ms / 1e3), "uqi_subset_images": n_uqi}}
 
 
 # ------------------------------------------------------------------ serving

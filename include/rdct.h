@@ -134,6 +134,17 @@ RDCT_API rdct_status rdct_inverse(const float *Yc, int64_t nbw, int64_t nbh, int
 RDCT_API rdct_status rdct_mse_psnr(const rdct_plane *ref, const rdct_out *rec, double *mse, double *psnr,
                           rdct_stream stream);
 
+/* Universal quality index of a reconstruction (Sec. 3 reports it beside PSNR
+ * and MSE; its definition is in the work the paper cites): the mean over all
+ * 8 x 8 windows (sliding by one pixel) of
+ *   [2 s_xy / (s_x^2 + s_y^2)] * [2 mx my / (mx^2 + my^2)]
+ * with window means, unbiased variances and covariance; a factor whose
+ * denominator is zero counts as 1 (the paper gives no window size; 8 x 8 and
+ * the flat-window rule are readings).  rec->u8 is used when non-NULL (exact
+ * integer window sums), else rec->f32.  *q is a DEVICE double.  The plane
+ * must be at least 8 x 8. */
+RDCT_API rdct_status rdct_uqi(const rdct_plane *ref, const rdct_out *rec, double *q, rdct_stream stream);
+
 /* The whole path in one kernel (Sec. 3): forward, keep r zigzag
  * coefficients with the S scaling, inverse, squared error.  `out` may be
  * NULL (error only).  *sse (DEVICE double) receives the sum over pixels of

@@ -76,6 +76,7 @@ def _load():
         lib.rdct_ref_sweep.argtypes = [u8p, i64, i32, i32, i32, dp, i32]
         lib.rdct_ref_sse.argtypes = [u8p, i64, i32, i32, u8p, dp, i64, dp]
         lib.rdct_ref_max_threads.argtypes = []
+        lib.rdct_ref_uqi.argtypes = [u8p, i64, i32, i32, u8p, dp, i64, i32, dp]
         _lib = lib
         return lib
 
@@ -223,6 +224,24 @@ def sse(ref: np.ndarray, rec: np.ndarray) -> float:
         st = lib.rdct_ref_sse(_ptr(ref, ctypes.c_uint8), pitch, w, h, None, _ptr(rec, ctypes.c_double),
                               rec.shape[1], _ptr(out, ctypes.c_double))
     _check(st, "sse")
+    return float(out[0])
+
+
+def uqi(ref: np.ndarray, rec: np.ndarray, window: int = 8) -> float:
+    """UQI (Wang & Bovik, cited in Sec. 3): mean over sliding window x window windows of
+    [2 s_xy / (s_x^2 + s_y^2)] [2 mx my / (mx^2 + my^2)] (a factor with a zero denominator is 1)."""
+    ref, pitch, w, h = _plane(ref)
+    out = np.zeros(1)
+    lib = _load()
+    if rec.dtype == np.uint8:
+        rec = np.ascontiguousarray(rec)
+        st = lib.rdct_ref_uqi(_ptr(ref, ctypes.c_uint8), pitch, w, h, _ptr(rec, ctypes.c_uint8), None,
+                              rec.shape[1], window, _ptr(out, ctypes.c_double))
+    else:
+        rec = np.ascontiguousarray(rec, dtype=np.float64)
+        st = lib.rdct_ref_uqi(_ptr(ref, ctypes.c_uint8), pitch, w, h, None, _ptr(rec, ctypes.c_double),
+                              rec.shape[1], window, _ptr(out, ctypes.c_double))
+    _check(st, "uqi")
     return float(out[0])
 
 

@@ -359,6 +359,56 @@ int rdct_ref_sse(const uint8_t *ref, int64_t pitch, int32_t w, int32_t h, const 
     return ORACLE_OK;
 }
 
+/* Universal quality index (the UQI of Sec. 3, defined in the work it cites,
+ * Wang & Bovik 2002): for every B x B window (sliding by one pixel) of the
+ * reference x and the reconstruction y,
+ *   Q = 4 s_xy mx my / ((s_x^2 + s_y^2)(mx^2 + my^2))
+ *     = [2 s_xy / (s_x^2 + s_y^2)] * [2 mx my / (mx^2 + my^2)]
+ * with sample means mx, my, unbiased variances s_x^2, s_y^2 and covariance
+ * s_xy; the index is the mean of Q over all windows.  Reading for flat
+ * windows: a factor whose denominator is zero is taken as 1 (its limit for
+ * equal windows).  Computed directly per window in double precision. */
+int rdct_ref_uqi(const uint8_t *ref, int64_t pitch, int32_t w, int32_t h, const uint8_t *rec_u8,
+                 const double *rec_f64, int64_t rec_pitch, int32_t B, double *q) {
+    if (!ref || !q || (!rec_u8 && !rec_f64) || B < 2 || w < B || h < B || pitch < w || rec_pitch < w)
+        return ORACLE_ERR_ARG;
+    const double n = (double)B * B;
+    double total = 0.0;
+    int64_t count = 0;
+    for (int64_t y0 = 0; y0 + B <= h; ++y0)
+        for (int64_t x0 = 0; x0 + B <= w; ++x0) {
+            double mx = 0, my = 0;
+            for (int i = 0; i < B; ++i)
+                for (int j = 0; j < B; ++j) {
+                    mx += ref[(y0 + i) * pitch + x0 + j];
+                    my += rec_u8 ? (double)rec_u8[(y0 + i) * rec_pitch + x0 + j]
+                                 : rec_f64[(y0 + i) * rec_pitch + x0 + j];
+                }
+            mx /= n;
+            my /= n;
+            double vx = 0, vy = 0, cxy = 0;
+            for (int i = 0; i < B; ++i)
+                for (int j = 0; j < B; ++j) {
+                    const double a = ref[(y0 + i) * pitch + x0 + j] - mx;
+                    const double b = (rec_u8 ? (double)rec_u8[(y0 + i) * rec_pitch + x0 + j]
+                                             : rec_f64[(y0 + i) * rec_pitch + x0 + j]) - my;
+                    vx += a * a;
+                    vy += b * b;
+                    cxy += a * b;
+                }
+            vx /= n - 1;
+            vy /= n - 1;
+            cxy /= n - 1;
+            const double d1 = vx + vy, d2 = mx * mx + my * my;
+            const double f1 = d1 == 0.0 ? 1.0 : 2.0 * cxy / d1;
+            const double f2 = d2 == 0.0 ? 1.0 : 2.0 * mx * my / d2;
+            total += f1 * f2;
+            ++count;
+        }
+    *q = total / (double)count;
+    return ORACLE_OK;
+}
+
 int rdct_ref_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

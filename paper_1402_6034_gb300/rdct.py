@@ -96,6 +96,7 @@ _SIGS = {
     "rdct_inverse": [_vp, _i64, _i64, _i32, ctypes.c_int, ctypes.POINTER(Out), _vp],
     "rdct_mse_psnr": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp, _vp],
     "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
+    "rdct_uqi": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp],
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_sweep_noalloc": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_batch_plan_create": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), ctypes.POINTER(_vp)],
@@ -231,6 +232,8 @@ def mse_psnr(ref: torch.Tensor, rec: torch.Tensor, stream=None):
     """(MSE, PSNR) of rec (uint8 or float32 plane) against ref, as device float64 scalars."""
     p = plane_of(ref)
     _require_cuda(rec, "rec")
+    if rec.dim() != 2 or tuple(rec.shape) != tuple(ref.shape) or rec.stride(1) != 1:
+        raise ValueError("rec must be a 2-D plane of ref's shape with unit column stride")
     if rec.dtype == torch.uint8:
         out = Out(rec.data_ptr(), None, rec.stride(0), 0)
     elif rec.dtype == torch.float32:
@@ -241,6 +244,23 @@ def mse_psnr(ref: torch.Tensor, rec: torch.Tensor, stream=None):
     _check(load().rdct_mse_psnr(ctypes.byref(p), ctypes.byref(out), res.data_ptr(), res.data_ptr() + 8,
                                 _stream(stream)), "rdct_mse_psnr")
     return res[0], res[1]
+
+
+def uqi(ref: torch.Tensor, rec: torch.Tensor, stream=None) -> torch.Tensor:
+    """Universal quality index of rec (uint8 or float32 plane) against ref; device float64 scalar."""
+    p = plane_of(ref)
+    _require_cuda(rec, "rec")
+    if rec.dim() != 2 or tuple(rec.shape) != tuple(ref.shape) or rec.stride(1) != 1:
+        raise ValueError("rec must be a 2-D plane of ref's shape with unit column stride")
+    if rec.dtype == torch.uint8:
+        out = Out(rec.data_ptr(), None, rec.stride(0), 0)
+    elif rec.dtype == torch.float32:
+        out = Out(None, rec.data_ptr(), 0, rec.stride(0))
+    else:
+        raise ValueError("rec must be uint8 or float32")
+    q = torch.empty(1, dtype=torch.float64, device=ref.device)
+    _check(load().rdct_uqi(ctypes.byref(p), ctypes.byref(out), q.data_ptr(), _stream(stream)), "rdct_uqi")
+    return q[0]
 
 
 def fused(img: torch.Tensor, r: int, kind: int = KIND_RDCT, want_u8: bool = True, want_f32: bool = False,

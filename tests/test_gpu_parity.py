@@ -191,6 +191,34 @@ def test_mse_psnr(dev):
     assert m0.item() == 0.0 and p0.item() == float("inf")
 
 
+# ---------------------------------------------------------------------- UQI
+
+@pytest.mark.parametrize("h,w", [(8, 8), (72, 136), (512, 512), (264, 1000)])
+@pytest.mark.parametrize("r", [1, 6, 16])
+def test_uqi(dev, h, w, r):
+    img = _img(h, w, 90 + r)
+    xo, uo, _, _ = orc.fused(img, r)
+    t = to_dev(img, dev)
+    # uint8 reconstruction: exact integer window sums, only the mean's summation order differs
+    q = rdct.uqi(t, to_dev(uo, dev)).item()
+    assert q == pytest.approx(orc.uqi(img, uo), rel=1e-12, abs=1e-14)
+    # float reconstruction: the same float32 values on both sides, double window sums
+    xf = xo.astype(np.float32)
+    qf = rdct.uqi(t, to_dev(xf, dev)).item()
+    assert qf == pytest.approx(orc.uqi(img, xf.astype(np.float64)), rel=1e-9, abs=1e-12)
+
+
+def test_uqi_pitched_identity_and_flat(dev):
+    img = _img(72, 136, 95)
+    v = _padded(img, dev, 160)
+    assert rdct.uqi(v, v).item() == pytest.approx(1.0, abs=1e-15)
+    rec = _padded(orc.fused(img, 3)[1], dev, 144)
+    assert rdct.uqi(v, rec).item() == pytest.approx(orc.uqi(img, orc.fused(img, 3)[1]), rel=1e-12)
+    flat = torch.full((16, 16), 100, dtype=torch.uint8, device=dev)
+    half = torch.full((16, 16), 50, dtype=torch.uint8, device=dev)
+    assert rdct.uqi(flat, half).item() == pytest.approx(2 * 100 * 50 / (100 ** 2 + 50 ** 2), rel=1e-15)
+
+
 # -------------------------------------------------------------------- sweep
 
 @pytest.mark.parametrize("kind", [rdct.KIND_RDCT, rdct.KIND_DCT])

@@ -312,3 +312,76 @@ def test_threads_do_not_change_results():
     b = orc.fused(img, 10, nthreads=4)
     np.testing.assert_array_equal(a[1], b[1])
     assert a[2] == pytest.approx(b[2], rel=1e-12)
+
+
+# ----------------------------------------------------------- UQI (Sec. 3)
+
+def _uqi_brute(x, y, n=8):
+    """UQI straight from its statistics (numpy mean / var / cov, ddof = 1), window by window."""
+    x = x.astype(np.float64)
+    y = y.astype(np.float64)
+    h, w = x.shape
+    qs = []
+    for i in range(h - n + 1):
+        for j in range(w - n + 1):
+            a, b = x[i:i + n, j:j + n].ravel(), y[i:i + n, j:j + n].ravel()
+            c = np.cov(a, b)
+            ma, mb = a.mean(), b.mean()
+            d1, d2 = c[0, 0] + c[1, 1], ma * ma + mb * mb
+            f1 = 1.0 if d1 == 0 else 2 * c[0, 1] / d1
+            f2 = 1.0 if d2 == 0 else 2 * ma * mb / d2
+            qs.append(f1 * f2)
+    return float(np.mean(qs)), len(qs)
+
+
+def test_uqi_identity_and_range():
+    x = synth.image_1f(40, 48, seed=3)
+    assert orc.uqi(x, x) == pytest.approx(1.0, abs=1e-15)
+    xo, uo, _, _ = orc.fused(x, 6)
+    q = orc.uqi(x, uo)
+    assert -1.0 <= q < 1.0
+
+
+@pytest.mark.parametrize("a", [0.5, 2.0, 3.0])
+def test_uqi_scaled_copy_closed_form(a):
+    # y = a x: each factor is 2a / (1 + a^2) in every window with nonzero mean and variance
+    x = synth.random_bytes((24, 32), seed=4).astype(np.uint8) | 1
+    q = orc.uqi(x, a * x.astype(np.float64))
+    assert q == pytest.approx(4 * a * a / (1 + a * a) ** 2, rel=1e-12)
+
+
+def test_uqi_shift_and_negation_closed_form():
+    from scipy.ndimage import uniform_filter
+    x = synth.image_1f(30, 37, seed=5).astype(np.float64)
+    m = uniform_filter(x, size=8, mode="constant")  # centred 8x8 window means
+    m = m[4:x.shape[0] - 3, 4:x.shape[1] - 3]        # the (h-7) x (w-7) full windows
+    assert m.shape == (23, 30)
+    c = 17.0
+    # y = x + c: the structure factor is 1, the luminance factor depends on the window mean
+    exp = np.mean(2 * m * (m + c) / (m * m + (m + c) ** 2))
+    assert orc.uqi(x.astype(np.uint8), x + c) == pytest.approx(exp, rel=1e-12)
+    # y = 255 - x: the structure factor is -1 wherever the window is not flat
+    exp = np.mean(-2 * m * (255 - m) / (m * m + (255 - m) ** 2))
+    assert orc.uqi(x.astype(np.uint8), 255.0 - x) == pytest.approx(exp, rel=1e-12)
+
+
+def test_uqi_flat_windows():
+    x = np.full((8, 8), 100, np.uint8)
+    assert orc.uqi(x, np.full((8, 8), 100, np.uint8)) == 1.0
+    # flat against flat: structure factor 1 by the zero-denominator rule, luminance 2cd/(c^2+d^2)
+    assert orc.uqi(x, np.full((8, 8), 50, np.uint8)) == pytest.approx(2 * 100 * 50 / (100 ** 2 + 50 ** 2))
+    z = np.zeros((9, 9), np.uint8)
+    assert orc.uqi(z, z) == 1.0
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (9, 13), (16, 11)])
+def test_uqi_brute_force_and_symmetry(shape):
+    x = synth.random_bytes(shape, seed=6).astype(np.uint8)
+    y = synth.random_bytes(shape, seed=7).astype(np.uint8)
+    x[:, :3] = 40  # some flat-ish windows and correlated content
+    y[:, :3] = 40
+    y[2:, 4:] = x[2:, 4:] // 2 + 30
+    q_ref, nwin = _uqi_brute(x, y)
+    assert nwin == (shape[0] - 7) * (shape[1] - 7)
+    assert orc.uqi(x, y) == pytest.approx(q_ref, rel=1e-12, abs=1e-14)
+    assert orc.uqi(y, x) == pytest.approx(orc.uqi(x, y), rel=1e-14)
