@@ -9,7 +9,9 @@ from Sec. 2-3 of Cintra & Bayer, "A DCT Approximation for Image Compression")
 and wraps it with numpy.  It also holds the paper's spectral analysis (the
 transfer functions H_m, the error D_m and the error energy eps_m of Sec. 2,
 Table 2), the quality measures of Sec. 3 (MSE, PSNR, their averages over
-images, the absolute percentage error against the exact DCT) and nothing else.
+images, the absolute percentage error against the exact DCT, the UQI) and the
+matrices of the other transforms the paper names (the signed DCT of Sec. 3 and
+the floor / ceiling generalisations of its conclusion).
 
 Parity status: every function below is pinned by a test in
 ``tests/test_oracle_pins.py`` against something other than itself (printed
@@ -77,6 +79,7 @@ def _load():
         lib.rdct_ref_sse.argtypes = [u8p, i64, i32, i32, u8p, dp, i64, dp]
         lib.rdct_ref_max_threads.argtypes = []
         lib.rdct_ref_uqi.argtypes = [u8p, i64, i32, i32, u8p, dp, i64, i32, dp]
+        lib.rdct_ref_fused_general.argtypes = [u8p, i64, i32, i32, i32, dp, dp, dp, u8p, dp, dp, i32]
         _lib = lib
         return lib
 
@@ -146,6 +149,64 @@ def zigzag() -> np.ndarray:
 def sdct_matrix() -> np.ndarray:
     """The signed DCT of the comparison in Sec. 2 (Table 2), read as sign(C)/sqrt(8)."""
     return np.sign(dct_matrix()) / np.sqrt(8.0)
+
+
+# ---------------------------------------------------------- other transforms
+
+VARIANTS = ("round", "ceil", "floor", "sdct", "sdct_polar")
+
+
+def variant_matrices(name: str):
+    """(F, G) for the 2-D experiment of Sec. 3: a block A goes to F A F^T and comes back as G Yhat G^T.
+
+    round      -- C_orth of Sec. 2: [2C] with round-off, times (C0 C0^T)^(-1/2); G = F^T.
+    ceil/floor -- the conclusion's generalisations: ceil(2C) / floor(2C) in place of [2C], orthogonalised the
+                  same way (polar factor (T T^T)^(-1/2) T); floor(2C) has a zero first row, so T T^T is singular
+                  and no such factor exists (ValueError).
+    sdct       -- the signed DCT compared in Sec. 3, sign(C) / sqrt(8) (the scaling of Table 2), rebuilt with
+                  its exact inverse G = F^(-1).
+    sdct_polar -- sign(C) orthogonalised like C0; G = F^T.
+    """
+    C = dct_matrix()
+    if name == "round":
+        T = round_off_matrix()
+    elif name == "ceil":
+        T = np.ceil(2.0 * C)
+    elif name == "floor":
+        T = np.floor(2.0 * C)
+    elif name in ("sdct", "sdct_polar"):
+        T = np.sign(C)
+    else:
+        raise ValueError(f"unknown variant {name!r}")
+    if name == "sdct":
+        F = T / np.sqrt(8.0)
+        return F, np.linalg.inv(F)
+    gram = T @ T.T
+    lam, V = np.linalg.eigh(gram)
+    if lam.min() <= 1e-9 * lam.max():
+        raise ValueError(f"variant {name!r}: T T^T is singular, no orthogonal polar factor")
+    S = V @ np.diag(lam ** -0.5) @ V.T
+    F = S @ T
+    return F, F.T
+
+
+def fused_general(img: np.ndarray, r: int, F: np.ndarray, G: np.ndarray, want_xhat: bool = True,
+                  want_u8: bool = True, nthreads: int = 0):
+    """Sec. 3 with Y = F A F^T and X = G Yhat G^T; returns (xhat or None, u8 or None, sse, sse_u8)."""
+    img, pitch, w, h = _plane(img)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    xhat = np.zeros((h, w)) if want_xhat else None
+    u8 = np.zeros((h, w), dtype=np.uint8) if want_u8 else None
+    sse = np.zeros(1)
+    sse_u8 = np.zeros(1)
+    _check(_load().rdct_ref_fused_general(_ptr(img, ctypes.c_uint8), pitch, w, h, r, _ptr(F, ctypes.c_double),
+                                          _ptr(G, ctypes.c_double),
+                                          _ptr(xhat, ctypes.c_double) if xhat is not None else None,
+                                          _ptr(u8, ctypes.c_uint8) if u8 is not None else None,
+                                          _ptr(sse, ctypes.c_double), _ptr(sse_u8, ctypes.c_double), nthreads),
+           "fused_general")
+    return xhat, u8, float(sse[0]), float(sse_u8[0])
 
 
 # ------------------------------------------------------------- block pipeline

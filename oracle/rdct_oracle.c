@@ -16,6 +16,11 @@
  *                 DCT baseline); keep the first r coefficients of the standard
  *                 zigzag sequence, zero the rest; reconstruct with the inverse
  *                 (M orthogonal => inverse is M^T Yhat M); score with PSNR/MSE.
+ *   Sec. 3-4 the same experiment for any forward matrix F and reconstruction
+ *                 matrix G (rdct_ref_fused_general): the signed DCT compared
+ *                 in Sec. 3 and the floor / ceiling generalisations that the
+ *                 conclusion (Sec. 4) proposes; oracle.py builds the matrices.
+ *   Sec. 3   UQI (the quality index cited there) on 8 x 8 sliding windows.
  *
  * Style: direct triple-loop 8x8 matrix products in double precision, in the
  * order the paper states them.  No butterflies, no fused scaling, no blocking.
@@ -308,6 +313,59 @@ int rdct_ref_fused(const uint8_t *img, int64_t pitch, int32_t w, int32_t h, int3
             forward_block(M, A, Y);
             zonal_mask(zz, r, Y, Yh);
             inverse_block(M, Yh, X);
+            for (int i = 0; i < 8; ++i)
+                for (int j = 0; j < 8; ++j) {
+                    double x = X[i * 8 + j], a = A[i * 8 + j];
+                    int64_t o = (by * 8 + i) * (int64_t)w + bx * 8 + j;
+                    acc += (x - a) * (x - a);
+                    uint8_t q = to_u8(x);
+                    acc_u8 += ((double)q - a) * ((double)q - a);
+                    if (xhat) xhat[o] = x;
+                    if (u8) u8[o] = q;
+                }
+        }
+    }
+    (void)nthreads;
+    *sse = acc;
+    if (sse_u8) *sse_u8 = acc_u8;
+    return ORACLE_OK;
+}
+
+/* The Sec. 3 experiment with any pair of 8x8 matrices: each block A goes to
+ * Y = F A F^T, keeps the first r zigzag coefficients, and is rebuilt as
+ * X = G Yhat G^T.  This serves the generalisations of the conclusion (C0
+ * built with floor or ceiling instead of round-off, orthogonalised by the
+ * polar factor of Sec. 2) and the signed DCT compared in Sec. 3, whose
+ * matrices the caller supplies (row-major).  Same outputs as rdct_ref_fused.
+ * Pinned by the Kronecker form vec(F A F^T) = (F kron F) vec(A) on small
+ * planes, exact reconstruction at r = 64 and agreement with rdct_ref_fused
+ * for C_orth. */
+int rdct_ref_fused_general(const uint8_t *img, int64_t pitch, int32_t w, int32_t h, int32_t r, const double *F,
+                           const double *G, double *xhat, uint8_t *u8, double *sse, double *sse_u8,
+                           int32_t nthreads) {
+    int st = check_plane(img, pitch, w, h);
+    if (st) return st;
+    if (r < 1 || r > 64 || !sse || !F || !G) return ORACLE_ERR_ARG;
+    double Ft[64], Gt[64];
+    transpose8(F, Ft);
+    transpose8(G, Gt);
+    int zz[64];
+    oracle_zigzag(zz);
+    int64_t nbw = w / 8, nbh = h / 8;
+    double acc = 0.0, acc_u8 = 0.0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(static) reduction(+ : acc, acc_u8) num_threads(nt)
+#endif
+    for (int64_t by = 0; by < nbh; ++by) {
+        for (int64_t bx = 0; bx < nbw; ++bx) {
+            double A[64], tmp[64], Y[64], Yh[64], X[64];
+            load_block(img, pitch, by, bx, A);
+            matmul8(F, A, tmp);
+            matmul8(tmp, Ft, Y);
+            zonal_mask(zz, r, Y, Yh);
+            matmul8(G, Yh, tmp);
+            matmul8(tmp, Gt, X);
             for (int i = 0; i < 8; ++i)
                 for (int j = 0; j < 8; ++j) {
                     double x = X[i * 8 + j], a = A[i * 8 + j];

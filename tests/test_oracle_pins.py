@@ -385,3 +385,86 @@ def test_uqi_brute_force_and_symmetry(shape):
     assert nwin == (shape[0] - 7) * (shape[1] - 7)
     assert orc.uqi(x, y) == pytest.approx(q_ref, rel=1e-12, abs=1e-14)
     assert orc.uqi(y, x) == pytest.approx(orc.uqi(x, y), rel=1e-14)
+
+
+# ------------------------------------------- variants (conclusion; SDCT of Sec. 3)
+
+def _zz_table():
+    return np.array([int(v) for row in load_golden("zigzag_jpeg.txt") for v in row])
+
+
+def _kron_reference(img, r, F, G):
+    """Every block through vec(Y) = (F kron F) vec(A), the JPEG-order zonal mask and vec(X) = (G kron G) vec(Yhat)."""
+    KF, KG = np.kron(F, F), np.kron(G, G)
+    keep = np.zeros(64, bool)
+    keep[_zz_table()[:r]] = True
+    h, w = img.shape
+    out = np.zeros((h, w))
+    for by in range(h // 8):
+        for bx in range(w // 8):
+            a = img[by * 8:by * 8 + 8, bx * 8:bx * 8 + 8].astype(np.float64).ravel()
+            y = KF @ a
+            out[by * 8:by * 8 + 8, bx * 8:bx * 8 + 8] = (KG @ np.where(keep, y, 0.0)).reshape(8, 8)
+    return out
+
+
+def test_variant_round_is_c_orth():
+    F, G = orc.variant_matrices("round")
+    np.testing.assert_allclose(F, orc.orth_matrix(), atol=1e-15)
+    np.testing.assert_allclose(G, F.T, atol=0)
+    img = synth.image_1f(24, 32, seed=8)
+    for r in (1, 10, 45):
+        xg, ug, sg, _ = orc.fused_general(img, r, F, G)
+        xo, uo, so, _ = orc.fused(img, r)
+        np.testing.assert_allclose(xg, xo, atol=1e-10)
+        assert sg == pytest.approx(so, rel=1e-10)
+
+
+@pytest.mark.parametrize("name", ["ceil", "sdct_polar"])
+def test_variant_polar_factor(name):
+    import scipy.linalg
+    C = orc.dct_matrix()
+    T = np.ceil(2 * C) if name == "ceil" else np.sign(C)
+    F, G = orc.variant_matrices(name)
+    np.testing.assert_allclose(F @ F.T, np.eye(8), atol=1e-13)
+    np.testing.assert_array_equal(G, F.T)
+    # the orthogonal factor of the polar decomposition T = P U (scipy's SVD route, not the eigen route)
+    U, P = scipy.linalg.polar(T, side="left")
+    np.testing.assert_allclose(F, U, atol=1e-12)
+    # F T^T = P is symmetric positive definite
+    Pm = F @ T.T
+    np.testing.assert_allclose(Pm, Pm.T, atol=1e-12)
+    assert np.linalg.eigvalsh((Pm + Pm.T) / 2).min() > 0
+
+
+def test_variant_matrices_structure():
+    C = orc.dct_matrix()
+    # ceil(2C): first row all ones (2/sqrt(8) < 1), every other entry 0 or 1 (|2C| < 1 off the first row)
+    Tc = np.ceil(2 * C)
+    assert (Tc[0] == 1).all() and set(np.unique(Tc[1:])) == {0.0, 1.0}
+    # floor(2C): the first row is zero, so T T^T is singular and the variant is rejected
+    assert (np.floor(2 * C)[0] == 0).all()
+    with pytest.raises(ValueError):
+        orc.variant_matrices("floor")
+    # the signed DCT: the Table 2 matrix, rebuilt by its exact inverse
+    F, G = orc.variant_matrices("sdct")
+    np.testing.assert_array_equal(F, orc.sdct_matrix())
+    np.testing.assert_allclose(G @ F, np.eye(8), atol=1e-14)
+    # its even rows are orthogonal with norm 1 after the 1/sqrt(8) scaling; its odd rows are not
+    Gm = F @ F.T
+    np.testing.assert_allclose(Gm[::2, ::2], np.eye(4), atol=1e-15)
+    assert abs(Gm[1, 3]) == pytest.approx(0.5)
+
+
+@pytest.mark.parametrize("name", ["round", "ceil", "sdct", "sdct_polar"])
+def test_fused_general_against_kronecker_form(name):
+    F, G = orc.variant_matrices(name)
+    img = synth.random_bytes((16, 24), seed=9)
+    for r in (1, 7, 30, 64):
+        ref = _kron_reference(img, r, F, G)
+        xg, ug, sg, su = orc.fused_general(img, r, F, G)
+        np.testing.assert_allclose(xg, ref, atol=1e-9)
+        assert sg == pytest.approx(float(((ref - img) ** 2).sum()), rel=1e-9, abs=1e-12)
+        np.testing.assert_array_equal(ug, np.clip(np.rint(xg), 0, 255).astype(np.uint8))
+    # r = 64 keeps everything: exact reconstruction (G F = I)
+    assert orc.fused_general(img, 64, F, G)[2] < 1e-18 * img.size * 255 ** 2
