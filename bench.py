@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["video", "batch512", "uneven", "sweep"], default="video")
+    ap.add_argument("--workload", choices=["video", "batch512", "uneven", "sweep", "variants"], default="video")
     ap.add_argument("--frames", type=int, default=600)
     ap.add_argument("--r", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -393,6 +393,74 @@ def bench_sweep(args, dev):
                            "windows_per_s": 505 * 505 / (uqi_ms / 1e3), "uqi_subset_images": n_uqi}}
 
 
+def variant_ops_per_block(r: int) -> int:
+    """FP32 operations the variant kernel needs per 8x8 block at r (one FMA or add = 1): forward row pass
+    (8 rows x K kept columns x 8), column pass over the kept zone (zone x 8), inverse (8 x zone, then
+    64 x K), squared error (64 subtractions + 64 FMAs).  D is the anti-diagonal class of r, K = min(D+1, 8)."""
+    zz = sorted(((i + j, i if (i + j) % 2 else j, i, j) for i in range(8) for j in range(8)))
+    d = zz[r - 1][0]
+    k = min(d + 1, 8)
+    zone = sum(1 for i in range(8) for j in range(8) if i + j <= d)
+    return 8 * k * 8 + zone * 8 + 8 * zone + 64 * k + 128
+
+
+def bench_variants(args, dev):
+    """The other transforms of the paper (signed DCT, ceil(2C) polar variant, sign(C) polar, and C_orth
+    through the same general kernel) on the 1024 x 512^2 batch at r = 10, timed as one tall plane per call;
+    average PSNR and UQI per variant over a 64-image subset at several r."""
+    from paper_1402_6034_gb300 import rdct, synth
+    n, r = 1024, 10
+    base = torch.from_numpy(synth.image_batch(64, 512, 512, 2.0, 0)).to(dev)
+    imgs = torch.cat([torch.roll(base, shifts=(8 * k, 8 * ((k * 7) % 64)), dims=(1, 2)) for k in range(n // 64)])
+    tall = imgs.view(n * 512, 512)
+    out = torch.empty_like(tall)
+    sse = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    names = ["round", "ceil", "sdct", "sdct_polar"]
+    per = {}
+    clock = 2070.0
+    ops_px = variant_ops_per_block(r) / 64.0
+    for name in names:
+        v = rdct.VARIANTS[name]
+        p = rdct.plane_of(tall)
+        o = rdct.Out(out.data_ptr(), None, 512, 0)
+        lib = rdct.load()
+
+        def step():
+            rdct._check(lib.rdct_fused_variant(ctypes.byref(p), r, v, ctypes.byref(o), sse.data_ptr(),
+                                               stream.cuda_stream), "rdct_fused_variant")
+
+        ms = events_time(step, args.steps, args.warmup, stream)
+        gpx = n * 512 * 512 / (ms / 1e3) / 1e9
+        per[name] = {"gpixel_s": gpx, "ms": ms, "psnr_db_of_batch_mse": float(10 * np.log10(255.0 ** 2 * n * 512 * 512
+                                                                                          / sse.item()))}
+    quality = {}
+    for rr in (5, 10, 16, 32, 45):
+        row = {}
+        for name in names:
+            ps, qs = [], []
+            for i in range(64):
+                u8, _, s1 = rdct.fused_variant(imgs[i], rr, rdct.VARIANTS[name], stream=stream)
+                ps.append(10 * torch.log10(255.0 ** 2 * 512 * 512 / s1))
+                qs.append(rdct.uqi(imgs[i], u8, stream=stream))
+            row[name] = {"psnr_db": float(torch.stack(ps).mean()), "uqi": float(torch.stack(qs).mean())}
+        quality[str(rr)] = row
+    peak = 152 * 128 * clock * 1e6 / 1e12  # FP32 lane-operations per second, in T/s
+    achieved = per["ceil"]["gpixel_s"] * 1e9 * ops_px / 1e12
+    return {"metric": METRIC, "value": per["ceil"]["gpixel_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per["ceil"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": "variants_1024x512x512_r10", "images": n, "r": r,
+                       "timed": "one rdct_fused_variant call on the batch as one 512 x 524288 plane",
+                       "value_is": "ceil(2C) polar variant"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "ops_per_pixel": ops_px,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (one FMA = one op)"},
+            "gpu_launches": 2 * args.steps, "per_variant": per, "quality_64_images": quality}
+
+
+# ------------------------------------------------------------------ serving
 # ------------------------------------------------------------------ serving
 
 def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0), seed: int = 0):
@@ -512,8 +580,8 @@ def main():
     from paper_1402_6034_gb300 import rdct
     rdct.load()
 
-    if args.workload in ("uneven", "sweep"):
-        line = (bench_uneven if args.workload == "uneven" else bench_sweep)(args, dev)
+    if args.workload in ("uneven", "sweep", "variants"):
+        line = {"uneven": bench_uneven, "sweep": bench_sweep, "variants": bench_variants}[args.workload](args, dev)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

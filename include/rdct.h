@@ -134,6 +134,42 @@ RDCT_API rdct_status rdct_inverse(const float *Yc, int64_t nbw, int64_t nbh, int
 RDCT_API rdct_status rdct_mse_psnr(const rdct_plane *ref, const rdct_out *rec, double *mse, double *psnr,
                           rdct_stream stream);
 
+/* The other transforms the paper names, run through the same block experiment
+ * (Sec. 3: Y = F A F^T, keep the first r zigzag coefficients, rebuild as
+ * X = G Yhat G^T, score the squared error):
+ *   ROUND       C_orth of Sec. 2 (the proposed transform; the general FP32
+ *               kernel, a cross-check of the integer path);
+ *   CEIL/FLOOR  the generalisations of the conclusion (Sec. 4): ceil(2C) or
+ *               floor(2C) in place of [2C], orthogonalised the way Sec. 2
+ *               orthogonalises C0 (the polar factor (T T^T)^(-1/2) T), G = F^T.
+ *               floor(2C) has a zero first row, so it has no such factor and
+ *               every call with FLOOR returns RDCT_ERR_ARG;
+ *   SDCT        the signed DCT of the comparison in Sec. 3, sign(C)/sqrt(8)
+ *               (the scaling of Table 2), rebuilt with its exact inverse
+ *               (sign(C) is not orthogonal);
+ *   SDCT_POLAR  sign(C) orthogonalised like C0, G = F^T.
+ * The paper gives no compression inverse for these; the ones above are the
+ * readings. */
+typedef enum {
+    RDCT_VARIANT_ROUND = 0,
+    RDCT_VARIANT_CEIL = 1,
+    RDCT_VARIANT_FLOOR = 2,
+    RDCT_VARIANT_SDCT = 3,
+    RDCT_VARIANT_SDCT_POLAR = 4
+} rdct_variant;
+
+/* The variant's forward matrix F and reconstruction matrix G, 64 doubles each,
+ * row-major, written to HOST memory (computed on the host in double). */
+RDCT_API rdct_status rdct_variant_matrices(rdct_variant v, double *F, double *G);
+
+/* The whole experiment for one plane and one variant in one kernel (FP32
+ * products, one thread per block): reconstruction to out (uint8
+ * clamp(round(X)) and/or FP32 X, either may be NULL) and the plane's squared
+ * error sum (X - A)^2 to *sse, a DEVICE double (8-byte aligned).  1 <= r <= 64.
+ * Plane rules as for rdct_fused. */
+RDCT_API rdct_status rdct_fused_variant(const rdct_plane *src, int32_t r, rdct_variant v, const rdct_out *out,
+                                        double *sse, rdct_stream stream);
+
 /* Universal quality index of a reconstruction (Sec. 3 reports it beside PSNR
  * and MSE; its definition is in the work the paper cites): the mean over all
  * 8 x 8 windows (sliding by one pixel) of

@@ -51,6 +51,16 @@ struct DctConsts {
 struct ScaleConsts {
     float dd[64];
 };
+// Forward and reconstruction matrices of the other transforms (signed DCT,
+// floor / ceiling variants): a block A goes to F A F^T and back as G Yhat G^T.
+struct MatConsts {
+    float f[64];  // F, row-major
+    float g[64];  // G, row-major
+};
+template <int D>
+cudaError_t launch_variant_d(const JobDesc &job, const MatConsts &M, double *acc, cudaStream_t s);
+// F and G of a variant in double (host); RDCT_ERR_ARG for floor(2C) (singular).
+rdct_status variant_matrices(rdct_variant v, double F[8][8], double G[8][8]);
 
 // Error state (thread-local message).
 rdct_status set_error(rdct_status s, const std::string &msg);

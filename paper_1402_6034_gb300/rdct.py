@@ -17,6 +17,9 @@ from . import build_lib
 
 KIND_RDCT = 0
 KIND_DCT = 1
+# other transforms of the paper (rdct_variant)
+VARIANT_ROUND, VARIANT_CEIL, VARIANT_FLOOR, VARIANT_SDCT, VARIANT_SDCT_POLAR = 0, 1, 2, 3, 4
+VARIANTS = {"round": 0, "ceil": 1, "floor": 2, "sdct": 3, "sdct_polar": 4}
 
 _STATUS = {0: "ok", 1: "invalid argument", 2: "invalid shape", 3: "out of memory", 4: "too large",
            5: "CUDA error", 6: "timeout", 7: "busy", 8: "not found", 9: "cancelled"}
@@ -97,6 +100,8 @@ _SIGS = {
     "rdct_mse_psnr": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp, _vp],
     "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_uqi": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp],
+    "rdct_variant_matrices": [ctypes.c_int, _vp, _vp],
+    "rdct_fused_variant": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_sweep_noalloc": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_batch_plan_create": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), ctypes.POINTER(_vp)],
@@ -261,6 +266,31 @@ def uqi(ref: torch.Tensor, rec: torch.Tensor, stream=None) -> torch.Tensor:
     q = torch.empty(1, dtype=torch.float64, device=ref.device)
     _check(load().rdct_uqi(ctypes.byref(p), ctypes.byref(out), q.data_ptr(), _stream(stream)), "rdct_uqi")
     return q[0]
+
+
+def variant_matrices(variant: int):
+    """(F, G) of a variant as float64 numpy arrays [8, 8], computed by the library on the host."""
+    import numpy as np
+    F = np.zeros(64)
+    G = np.zeros(64)
+    _check(load().rdct_variant_matrices(variant, F.ctypes.data, G.ctypes.data), "rdct_variant_matrices")
+    return F.reshape(8, 8), G.reshape(8, 8)
+
+
+def fused_variant(img: torch.Tensor, r: int, variant: int, want_u8: bool = True, want_f32: bool = False,
+                  sse: torch.Tensor | None = None, stream=None):
+    """Block experiment with another transform (signed DCT, ceil/floor variants); returns (u8, f32, sse[1])."""
+    p = plane_of(img)
+    dev = img.device
+    u8 = torch.empty((p.h, p.w), dtype=torch.uint8, device=dev) if want_u8 else None
+    f32 = torch.empty((p.h, p.w), dtype=torch.float32, device=dev) if want_f32 else None
+    if sse is None:
+        sse = torch.empty(1, dtype=torch.float64, device=dev)
+    out = Out(u8.data_ptr() if u8 is not None else None, f32.data_ptr() if f32 is not None else None,
+              u8.stride(0) if u8 is not None else 0, p.w)
+    _check(load().rdct_fused_variant(ctypes.byref(p), r, variant, ctypes.byref(out), sse.data_ptr(),
+                                     _stream(stream)), "rdct_fused_variant")
+    return u8, f32, sse
 
 
 def fused(img: torch.Tensor, r: int, kind: int = KIND_RDCT, want_u8: bool = True, want_f32: bool = False,
