@@ -170,6 +170,16 @@ RDCT_API rdct_status rdct_variant_matrices(rdct_variant v, double *F, double *G)
 RDCT_API rdct_status rdct_fused_variant(const rdct_plane *src, int32_t r, rdct_variant v, const rdct_out *out,
                                         double *sse, rdct_stream stream);
 
+/* Spectral comparison of Sec. 2 (Fig. 2 and Table 2) for a variant's forward
+ * matrix T (C_orth for ROUND, sign(C)/sqrt(8) for SDCT): D_m(w) =
+ * |H_m(w; C) - H_m(w; T)|^2 with H_m(w; T) = sum_n t_{m,n} exp(-j n w), sampled
+ * at w_i = i pi / (npoints - 1), i = 0 .. npoints-1, into D[m * npoints + i]
+ * (HOST, 8 * npoints doubles, or NULL), and eps[m] = integral of D_m over
+ * [0, pi] by the composite Simpson rule on that grid (HOST, 8 doubles).
+ * npoints odd, 3 .. 2^24.  Host computation only (analysis, not the image
+ * path). */
+RDCT_API rdct_status rdct_spectral_error(rdct_variant v, int32_t npoints, double *D, double *eps);
+
 /* Universal quality index of a reconstruction (Sec. 3 reports it beside PSNR
  * and MSE; its definition is in the work the paper cites): the mean over all
  * 8 x 8 windows (sliding by one pixel) of

@@ -101,6 +101,7 @@ _SIGS = {
     "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_uqi": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp],
     "rdct_variant_matrices": [ctypes.c_int, _vp, _vp],
+    "rdct_spectral_error": [ctypes.c_int, _i32, _vp, _vp],
     "rdct_fused_variant": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_sweep_noalloc": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
@@ -275,6 +276,16 @@ def variant_matrices(variant: int):
     G = np.zeros(64)
     _check(load().rdct_variant_matrices(variant, F.ctypes.data, G.ctypes.data), "rdct_variant_matrices")
     return F.reshape(8, 8), G.reshape(8, 8)
+
+
+def spectral_error(variant: int, npoints: int = 20001, want_curves: bool = False):
+    """(eps [8], D [8, npoints] or None, omega [npoints]) of Sec. 2 for a variant's forward matrix (host)."""
+    import numpy as np
+    eps = np.zeros(8)
+    D = np.zeros((8, npoints)) if want_curves else None
+    _check(load().rdct_spectral_error(variant, npoints, D.ctypes.data if D is not None else None, eps.ctypes.data),
+           "rdct_spectral_error")
+    return eps, D, np.linspace(0.0, np.pi, npoints)
 
 
 def fused_variant(img: torch.Tensor, r: int, variant: int, want_u8: bool = True, want_f32: bool = False,
