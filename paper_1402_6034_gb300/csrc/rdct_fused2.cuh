@@ -2,9 +2,9 @@
 // transform, zonal truncation with the S scaling of Sec. 2, inverse, squared
 // error) shaped for sm_103a issue rates.
 //
-// Per 8x8 block (a thread owns two vertically adjacent blocks):
+// Per 8x8 block (a thread owns two vertically adjacent blocks, a and b):
 //   * rows of pixels arrive through a per-thread cp.async ring in shared
-//     memory (three stages in flight, no block barriers: each thread only
+//     memory (double-buffered, no block barriers: each thread only
 //     reads what it copied itself);
 //   * row pass: every output of C0 applied to a row is one pair of byte dot
 //     products (dp4a) of the packed pixels with a row of C0 as signed bytes,
@@ -14,8 +14,8 @@
 //   * compression: kept coefficients become Z = W Y with W = 576 d_i^2 d_j^2,
 //     converted exactly to FP32 in units of 2^-149 (subnormal range);
 //   * inverse: C0^T butterflies in FP32, exact because every value is an
-//     integer multiple of 2^-149 below 2^24 units; the column pass is scalar,
-//     the row pass runs on f32x2 pairs of rows;
+//     integer multiple of 2^-149 below 2^24 units; every value from here on is
+//     an f32x2 pair (block a, block b), so one instruction serves both blocks;
 //   * output: one f32x2 multiply by 1/576 leaves round(Xhat) in the bit
 //     pattern of each float (negative values carry the sign bit), and
 //     cvt.pack.sat clamps to [0, 255] and packs four pixels per two
@@ -62,6 +62,11 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
     return d;
 }
 
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
 
 // ------------------------------------------------------------ int helpers
 
@@ -82,27 +87,20 @@ __host__ __device__ constexpr int group_weight(int g) {
 
 // --------------------------------------------------------------- block body
 
-// One 8x8 block in rows w[0..7] (8 pixels each, little-endian); keeps every
-// anti-diagonal < D plus the ranks < r of diagonal D.  Writes the uint8
-// reconstruction when dst != nullptr; returns 576 * SSE of the block.
+// The two vertically adjacent blocks of a column pair at once: the forward
+// transform and the compression run per block in int32, and from the
+// compressed coefficients on every value is an f32x2 pair (block a, block b),
+// so each inverse butterfly and each output scaling serves both blocks.
+// wb is all zeros when the pair has only its upper block (has_b false): a
+// zero block contributes nothing to the error and is not stored.
 template <int D>
-__device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], int r, uint8_t *dst,
-                                                           int64_t dpitch, int dalign) {
-    unsigned sumsq = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        sumsq = __dp4a(w[i].x, w[i].x, sumsq);
-        sumsq = __dp4a(w[i].y, w[i].y, sumsq);
-    }
-    // row pass: R[i][k] = sum_n C0[k][n] A[i][n]
+__device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][8]) {
     int R[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int k = 0; k < 8; ++k)
             R[i][k] = dp4a_us(w[i].x, c0_row_word(k, 0), dp4a_us(w[i].y, c0_row_word(k, 1), 0));
-    // column pass: Y = C0 R
-    int Y[8][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int c[8], o[8];
@@ -112,24 +110,38 @@ __device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], 
 #pragma unroll
         for (int i = 0; i < 8; ++i) Y[i][j] = o[i];
     }
-    // compression: Z = W Y on the retained zone, as FP32 in units of 2^-149
+}
+
+template <int D>
+__device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], int r,
+                                                          uint8_t *dst, int64_t dpitch, int dalign, bool has_b) {
+    unsigned sumsq = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        sumsq = __dp4a(wa[i].x, wa[i].x, sumsq);
+        sumsq = __dp4a(wa[i].y, wa[i].y, sumsq);
+        sumsq = __dp4a(wb[i].x, wb[i].x, sumsq);
+        sumsq = __dp4a(wb[i].y, wb[i].y, sumsq);
+    }
+    int Ya[8][8], Yb[8][8];
+    forward_c0_int<D>(wa, Ya);
+    forward_c0_int<D>(wb, Yb);
+    // compression: Z = W Y on the retained zone, as f32x2 pairs in units of 2^-149
     unsigned g2[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-    float Z[8][8];
+    const f2 unit = f2_make(0x1p-149f, 0x1p-149f), bias = f2_make(-0x1.8p-126f, -0x1.8p-126f);
+    f2 Z[8][8];
     static_for<0, 8>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         static_for<0, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             if constexpr (i + j <= D) {
-                int y = Y[i][j];
+                int ya = Ya[i][j], yb = Yb[i][j];
                 if constexpr (i + j == D) {
-                    if (zz_rank(i, j) >= r) y = 0;
+                    if (zz_rank(i, j) >= r) ya = yb = 0;
                 }
-                g2[weight_group(i, j)] += (unsigned)(y * y);
-                // bits of 1.5 * 2^23 + W y; the fma rescales by 2^-149 exactly
-                const int zb = y * weight(i, j) + 0x4B400000;
-                Z[i][j] = __fmaf_rn(__int_as_float(zb), 0x1p-149f, -0x1.8p-126f);
-            } else {
-                Z[i][j] = 0.0f;
+                g2[weight_group(i, j)] += (unsigned)(ya * ya) + (unsigned)(yb * yb);
+                const int za = ya * weight(i, j) + 0x4B400000, zb = yb * weight(i, j) + 0x4B400000;
+                Z[i][j] = fma2(f2_make(__int_as_float(za), __int_as_float(zb)), unit, bias);
             }
         });
     });
@@ -138,44 +150,48 @@ __device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], 
     for (int g = 0; g < 6; ++g) kept += (unsigned long long)g2[g] * (unsigned)group_weight(g);
 
     if (dst != nullptr) {
-        // inverse columns: U = C0^T Z (scalar FP32)
-        float U[8][8];
+        // inverse columns: U = C0^T Z
+        f2 U[8][8];
         static_for<0, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
             constexpr unsigned m = col_mask(D, j);
             if constexpr (m != 0u) {
-                float in[8], out[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) in[i] = Z[i][j];
+                f2 in[8], out[8];
+                static_for<0, 8>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    if constexpr ((m >> i) & 1u) in[i] = Z[i][j];
+                    else in[i] = f2{0ull};
+                });
                 c0t_inverse<m>(in, out);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) U[i][j] = out[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) U[i][j] = 0.0f;
             }
         });
-        // inverse rows two at a time (f32x2), then round, clamp, pack, store
+        // inverse rows, then round, clamp, pack, store (row n of both blocks)
         constexpr unsigned rm = row_mask(D);
         const f2 inv576 = f2_make(1.0f / 576.0f, 1.0f / 576.0f);
 #pragma unroll
-        for (int n = 0; n < 8; n += 2) {
+        for (int n = 0; n < 8; ++n) {
             f2 in[8], E[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) in[j] = f2_make(U[n][j], U[n + 1][j]);
+            static_for<0, 8>([&](auto jc) {
+                constexpr int j = decltype(jc)::value;
+                if constexpr ((rm >> j) & 1u) in[j] = U[n][j];
+                else in[j] = f2{0ull};
+            });
             c0t_inverse<rm>(in, E);
             int qa[8], qb[8];
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                float a, b;
-                f2_split(mul2(E[m], inv576), a, b);
-                qa[m] = __float_as_int(a);
-                qb[m] = __float_as_int(b);
+                float x, y;
+                f2_split(mul2(E[m], inv576), x, y);
+                qa[m] = __float_as_int(x);
+                qb[m] = __float_as_int(y);
             }
             store_row_u8(dst + n * dpitch, dalign, pack4_sat(qa[0], qa[1], qa[2], qa[3]),
                          pack4_sat(qa[4], qa[5], qa[6], qa[7]));
-            store_row_u8(dst + (n + 1) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
-                         pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+            if (has_b)
+                store_row_u8(dst + (8 + n) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
+                             pack4_sat(qb[4], qb[5], qb[6], qb[7]));
         }
     }
     return 576ull * (unsigned long long)sumsq - kept;
@@ -191,7 +207,7 @@ __device__ __forceinline__ unsigned long long fused2_block(const uint2 (&w)[8], 
 template <int D>
 struct Fused2Shape {
     static constexpr int threads = 128;
-    static constexpr int min_blocks = D <= 8 ? 4 : 3;
+    static constexpr int min_blocks = D <= 7 ? 4 : 3;
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
@@ -342,20 +358,22 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
             cp_async_commit();
         }
         uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)cc.bx * 8 : nullptr;
-        // both blocks of the column pair, one after the other in the code but
-        // unrolled so that their independent work interleaves
+        // both blocks of the column pair together (the lower one all zeros
+        // when the plane ends after the upper one); lanes past the end of the
+        // plane (nblk == 0) fetched nothing and do nothing
+        if (nblk > 0) {
+            static_assert(kVRows == 2, "fused2_pair handles two blocks");
+            uint2 wa[8], wb[8];
+            const bool has_b = nblk == 2;
 #pragma unroll
-        for (int v = 0; v < kVRows; ++v) {
-            if (v < nblk) {
-                uint2 w[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
-                static_for<DLO, DHI + 1>([&](auto dc) {
-                    constexpr int d = decltype(dc)::value;
-                    if (cc.diag == d) s576 += fused2_block<d>(w, job.r, dst, job.dst_pitch, job.dalign);
-                });
+            for (int i = 0; i < 8; ++i) {
+                wa[i] = ring[((stage * kVRows + 0) * 8 + i) * THREADS + threadIdx.x];
+                wb[i] = has_b ? ring[((stage * kVRows + 1) * 8 + i) * THREADS + threadIdx.x] : make_uint2(0u, 0u);
             }
-            if (dst) dst += 8 * job.dst_pitch;
+            static_for<DLO, DHI + 1>([&](auto dc) {
+                constexpr int d = decltype(dc)::value;
+                if (cc.diag == d) s576 += fused2_pair<d>(wa, wb, job.r, dst, job.dst_pitch, job.dalign, has_b);
+            });
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
         const int img = job.image;
