@@ -34,7 +34,7 @@ UNIT = "Gpixel/s"
 # profiles/fused_video_40x4k_r16_ncu.md.  Reported only while the kernel sources still hash to
 # the value they had when the counters were taken.
 FUSED_TRAFFIC = {"sources_sha256_16": "9fff2710149a5ff8", "bytes_per_sample": 1.8936}
-FUSED_SOURCES = ["rdct_fused2.cuh", "rdct_device.cuh", "rdct_blocks.cuh", "rdct_fused2_batch.cu"]
+FUSED_SOURCES = ["rdct_fused2.cuh", "rdct_device.cuh", "rdct_blocks.cuh", "rdct_fused2_launch.cu"]
 
 
 def fused_sources_hash() -> str:

@@ -6,8 +6,7 @@
 // grouped into chunks, and the chunk table is walked by persistent warps, so a
 // batch of thousands of planes of different sizes and r costs one graph
 // launch.  The retained-coefficient count r varies per plane; chunks are
-// ordered by the anti-diagonal class of r so that neighbouring warps run the
-// same specialised code.
+// ordered by r and each r present gets its own specialised kernel launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -87,14 +86,14 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     const int per = p->tune.items_per_chunk;
     for (int32_t i = 0; i < njobs; ++i) {
         const int items = strips_of(p->jobs[i], vrows);
-        const int d = diag_class_host(p->jobs[i].r);
-        for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), d});
+        const int c = fused_class_of(p->jobs[i].r, p->tune.blocks_per_thread);
+        for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), c});
     }
-    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) { return a.diag < b.diag; });
+    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
     p->chunks = std::move(ch);
     const int bpt = p->tune.blocks_per_thread;
     for (int g = 0; g <= kBatchGroups; ++g) p->group_begin[g] = 0;
-    for (const Chunk &c : p->chunks) p->group_begin[batch_group_of_diag(c.diag, bpt) + 1]++;
+    for (const Chunk &c : p->chunks) p->group_begin[batch_group_of_class(c.cls, bpt) + 1]++;
     for (int g = 0; g < kBatchGroups; ++g) p->group_begin[g + 1] += p->group_begin[g];
 }
 

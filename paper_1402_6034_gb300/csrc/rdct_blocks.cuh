@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) fused_batch_kernel(const JobDesc *__restr
         unsigned long long s = 0;
         static_for<DLO, DHI + 1>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
-            if (ch.diag == d) s = run_chunk_rdct<d, OUT>(job, ch, lane);
+            if (ch.cls == d) s = run_chunk_rdct<d, OUT>(job, ch, lane);
         });
         s = warp_sum_u64(s);
         if (lane == 0 && s) atomicAdd(&acc[job.image], s);

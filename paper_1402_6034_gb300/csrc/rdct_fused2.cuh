@@ -87,13 +87,21 @@ __host__ __device__ constexpr int group_weight(int g) {
 
 // --------------------------------------------------------------- block body
 
-// The two vertically adjacent blocks of a column pair at once: the forward
-// transform and the compression run per block in int32, and from the
-// compressed coefficients on every value is an f32x2 pair (block a, block b),
-// so each inverse butterfly and each output scaling serves both blocks.
-// wb is all zeros when the pair has only its upper block (has_b false): a
-// zero block contributes nothing to the error and is not stored.
-template <int D>
+// Rows i holding retained coefficients in column j, and columns holding any,
+// when exactly the first R zigzag coefficients are kept.
+__host__ __device__ constexpr unsigned kept_col_mask(int R, int j) {
+    unsigned m = 0u;
+    for (int i = 0; i < 8; ++i)
+        if (zz_rank(i, j) < R) m |= 1u << i;
+    return m;
+}
+__host__ __device__ constexpr unsigned kept_row_mask(int R) {
+    unsigned m = 0u;
+    for (int j = 0; j < 8; ++j)
+        if (kept_col_mask(R, j) != 0u) m |= 1u << j;
+    return m;
+}
+
 __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][8]) {
     int R[8][8];
 #pragma unroll
@@ -112,9 +120,18 @@ __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][
     }
 }
 
-template <int D>
-__device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], int r,
-                                                          uint8_t *dst, int64_t dpitch, int dalign, bool has_b) {
+// The two vertically adjacent blocks of a column pair at once, keeping
+// exactly the first R zigzag coefficients (R is a compile-time constant, so
+// the compiler drops every forward output, conversion and inverse term that
+// r never keeps).  The forward transform and the compression run per block
+// in int32, and from the compressed coefficients on every value is an f32x2
+// pair (block a, block b), so each inverse butterfly and each output scaling
+// serves both blocks.  wb is all zeros when the pair has only its upper block
+// (has_b false): a zero block contributes nothing to the error and is not
+// stored.  Returns 576 * SSE of the two blocks.
+template <int R>
+__device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], uint8_t *dst,
+                                                          int64_t dpitch, int dalign, bool has_b) {
     unsigned sumsq = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -124,9 +141,9 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
         sumsq = __dp4a(wb[i].y, wb[i].y, sumsq);
     }
     int Ya[8][8], Yb[8][8];
-    forward_c0_int<D>(wa, Ya);
-    forward_c0_int<D>(wb, Yb);
-    // compression: Z = W Y on the retained zone, as f32x2 pairs in units of 2^-149
+    forward_c0_int(wa, Ya);
+    forward_c0_int(wb, Yb);
+    // compression: Z = W Y on the retained coefficients, as f32x2 pairs in units of 2^-149
     unsigned g2[6] = {0u, 0u, 0u, 0u, 0u, 0u};
     const f2 unit = f2_make(0x1p-149f, 0x1p-149f), bias = f2_make(-0x1.8p-126f, -0x1.8p-126f);
     f2 Z[8][8];
@@ -134,12 +151,10 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
         constexpr int i = decltype(ic)::value;
         static_for<0, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            if constexpr (i + j <= D) {
-                int ya = Ya[i][j], yb = Yb[i][j];
-                if constexpr (i + j == D) {
-                    if (zz_rank(i, j) >= r) ya = yb = 0;
-                }
+            if constexpr (zz_rank(i, j) < R) {
+                const int ya = Ya[i][j], yb = Yb[i][j];
                 g2[weight_group(i, j)] += (unsigned)(ya * ya) + (unsigned)(yb * yb);
+                // bits of 1.5 * 2^23 + W y; the fma rescales by 2^-149 exactly
                 const int za = ya * weight(i, j) + 0x4B400000, zb = yb * weight(i, j) + 0x4B400000;
                 Z[i][j] = fma2(f2_make(__int_as_float(za), __int_as_float(zb)), unit, bias);
             }
@@ -154,7 +169,7 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
         f2 U[8][8];
         static_for<0, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            constexpr unsigned m = col_mask(D, j);
+            constexpr unsigned m = kept_col_mask(R, j);
             if constexpr (m != 0u) {
                 f2 in[8], out[8];
                 static_for<0, 8>([&](auto ic) {
@@ -168,7 +183,7 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
             }
         });
         // inverse rows, then round, clamp, pack, store (row n of both blocks)
-        constexpr unsigned rm = row_mask(D);
+        constexpr unsigned rm = kept_row_mask(R);
         const f2 inv576 = f2_make(1.0f / 576.0f, 1.0f / 576.0f);
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
@@ -199,15 +214,15 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
 
 // ------------------------------------------------------------------ kernel
 
-// Launch shape per anti-diagonal class: 128 registers up to r = 45, 168
-// above, and at most kFused2MaxCtas CTAs of 128 threads per SM (see
-// launch_staged).  Measured: more registers for independent work per thread
-// beat more resident warps, and shared memory beyond four rings squeezes the
-// L1 the copies go through.
-template <int D>
+// Launch shape per r: 128 registers while r ends on an anti-diagonal up to 7
+// (r <= 36), 168 above, and at most kFused2MaxCtas CTAs of 128 threads per SM
+// (see launch_staged).  Measured: more registers for independent work per
+// thread beat more resident warps, and shared memory beyond four rings
+// squeezes the L1 the copies go through.
+template <int R>
 struct Fused2Shape {
     static constexpr int threads = 128;
-    static constexpr int min_blocks = D <= 7 ? 4 : 3;
+    static constexpr int min_blocks = diag_class(R) <= 7 ? 4 : 3;
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
@@ -240,7 +255,7 @@ __device__ __forceinline__ Chunk get_chunk(const Fused2Args &a, int c) {
         const int total = fused_items_of(a.single);
         const int it0 = c * a.chunk_items;
         const int n = total - it0 < a.chunk_items ? total - it0 : a.chunk_items;
-        return Chunk{0, it0, n, diag_class(a.single.r)};
+        return Chunk{0, it0, n, a.single.r - 1};
     } else {
         return a.chunks[c];
     }
@@ -255,7 +270,7 @@ __device__ __forceinline__ const JobDesc &get_job(const Fused2Args &a, int j) {
 // tracks its own column pair (row pair rp, block column bx), advanced by 32
 // per item without divisions.
 struct Cursor {
-    int c, left, job, diag, rp, bx;
+    int c, left, job, cls, rp, bx;
 };
 template <bool SINGLE>
 __device__ __forceinline__ void cursor_load(const Fused2Args &a, Cursor &cu, int lane) {
@@ -267,7 +282,7 @@ __device__ __forceinline__ void cursor_load(const Fused2Args &a, Cursor &cu, int
         cu.bx = L - cu.rp * nbw;
         cu.left = ch.nitems;
         cu.job = ch.job;
-        cu.diag = ch.diag;
+        cu.cls = ch.cls;
     }
 }
 template <bool SINGLE>
@@ -322,9 +337,9 @@ __device__ __forceinline__ void fetch_strip(const JobDesc &job, int rp, int bx, 
 
 // Persistent fused kernel: each lane owns kVRows vertically adjacent blocks of
 // every strip its warp visits; strips stream through a double-buffered
-// per-thread cp.async ring.  DLO..DHI are the anti-diagonal classes compiled in
-// (one class for single-plane launches).
-template <int DLO, int DHI, bool SINGLE, int THREADS, int MINB>
+// per-thread cp.async ring.  CLO..CHI are the launch classes compiled in
+// (class r - 1 keeps r coefficients; one class per launch).
+template <int CLO, int CHI, bool SINGLE, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args a) {
     __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
     const int lane = threadIdx.x & 31;
@@ -370,9 +385,9 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
                 wa[i] = ring[((stage * kVRows + 0) * 8 + i) * THREADS + threadIdx.x];
                 wb[i] = has_b ? ring[((stage * kVRows + 1) * 8 + i) * THREADS + threadIdx.x] : make_uint2(0u, 0u);
             }
-            static_for<DLO, DHI + 1>([&](auto dc) {
-                constexpr int d = decltype(dc)::value;
-                if (cc.diag == d) s576 += fused2_pair<d>(wa, wb, job.r, dst, job.dst_pitch, job.dalign, has_b);
+            static_for<CLO, CHI + 1>([&](auto cc_) {
+                constexpr int c = decltype(cc_)::value;
+                if (cc.cls == c) s576 += fused2_pair<c + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
             });
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
@@ -386,6 +401,20 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
         }
     }
     cp_async_wait<0>();
+}
+
+// Launch for exactly r = R retained coefficients: single-plane (a.single) or
+// batch (a.jobs / a.chunks).  Instantiated per R in rdct_fused2_r*.cu.
+template <int R>
+cudaError_t launch_fused2_r(const Fused2Args &a, bool single, int ctas_per_sm, cudaStream_t s) {
+    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
+    if (single)
+        launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+                      kFused2Smem, s, a);
+    else
+        launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+                      kFused2Smem, s, a);
+    return cudaGetLastError();
 }
 
 }  // namespace rdct

@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel for r = 1..8 (eight per translation
+// unit so that the 64 specialisations compile in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<1>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<2>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<3>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<4>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<5>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<6>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<7>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<8>(const Fused2Args &, bool, int, cudaStream_t);
+}  // namespace rdct

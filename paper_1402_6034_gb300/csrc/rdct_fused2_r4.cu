@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel for r = 33..40 (eight per translation
+// unit so that the 64 specialisations compile in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<33>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<34>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<35>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<36>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<37>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<38>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<39>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<40>(const Fused2Args &, bool, int, cudaStream_t);
+}  // namespace rdct

@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel for r = 41..48 (eight per translation
+// unit so that the 64 specialisations compile in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<41>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<42>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<43>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<44>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<45>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<46>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<47>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<48>(const Fused2Args &, bool, int, cudaStream_t);
+}  // namespace rdct

@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel for r = 49..56 (eight per translation
+// unit so that the 64 specialisations compile in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<49>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<50>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<51>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<52>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<53>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<54>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<55>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<56>(const Fused2Args &, bool, int, cudaStream_t);
+}  // namespace rdct

@@ -1,0 +1,14 @@
+// Instantiations of the fused kernel for r = 57..64 (eight per translation
+// unit so that the 64 specialisations compile in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<57>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<58>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<59>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<60>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<61>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<62>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<63>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<64>(const Fused2Args &, bool, int, cudaStream_t);
+}  // namespace rdct

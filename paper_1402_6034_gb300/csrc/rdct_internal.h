@@ -38,9 +38,11 @@ __host__ __device__ inline int32_t strips_of(const JobDesc &j, int vrows) {
     return vrows == kFusedVRows ? fused_items_of(j) : j.nbh * j.segs;
 }
 
-// A run of consecutive strips of one job handed to one warp.
+// A run of consecutive strips of one job handed to one warp.  cls is the
+// launch class of the job's r (fused_class_of): r - 1 for the two-block
+// kernel, the anti-diagonal class of r for the scalar kernel.
 struct Chunk {
-    int32_t job, item0, nitems, diag;
+    int32_t job, item0, nitems, cls;
 };
 
 // FP32 constants of the exact DCT (host-computed from cos in double).
@@ -95,11 +97,12 @@ cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double 
 // used as uint64 576*SSE for kind RDCT and as double SSE for kind DCT.
 cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps, cudaStream_t s);
 // Persistent batch kernels.  Chunks are grouped: with blocks_per_thread 2
-// one group per anti-diagonal class of r (15 groups, one specialised kernel
-// each), with blocks_per_thread 1 one group per register class (3 groups).
+// one group per r (64 groups, a kernel specialised for each r), with
+// blocks_per_thread 1 one group per register class (3 groups).
 // acc_u64[image] += 576 * SSE.  ctas_per_sm <= 0 uses the occupancy limit.
-constexpr int kBatchGroups = 15;
-int batch_group_of_diag(int d, int blocks_per_thread);
+constexpr int kBatchGroups = 64;
+int fused_class_of(int r, int blocks_per_thread);
+int batch_group_of_class(int cls, int blocks_per_thread);
 // blocks_per_thread 2 selects the dp4a/f32x2 kernel (128 threads per CTA,
 // strips of kFusedVRows block rows), 1 the scalar kernel with `warps` warps.
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
@@ -109,7 +112,7 @@ cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t
 cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, int ctas_per_sm, int chunk_items,
                                  cudaStream_t s);
 cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
-                                int d, int ctas_per_sm, cudaStream_t s);
+                                int r, int ctas_per_sm, cudaStream_t s);
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are

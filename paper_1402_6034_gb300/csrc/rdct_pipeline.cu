@@ -194,12 +194,12 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
             rdct_plane pl{s.d_in + b.off, j.w, j.w, b.rows};
             JobDesc d = make_job(pl, j.dst ? s.d_out + b.off : nullptr, j.w, nullptr, 0, j.r, j.image, 1);
             const int items = strips_of(d, kFusedVRows);
-            const int diag = diag_class_host(j.r);
+            const int cls = fused_class_of(j.r, 2);
             for (int it = 0; it < items; it += kItemsPerChunk)
-                cd.push_back(Chunk{(int32_t)jd.size(), it, std::min(kItemsPerChunk, items - it), diag});
+                cd.push_back(Chunk{(int32_t)jd.size(), it, std::min(kItemsPerChunk, items - it), cls});
             jd.push_back(d);
         }
-        std::stable_sort(cd.begin(), cd.end(), [](const Chunk &a, const Chunk &b) { return a.diag < b.diag; });
+        std::stable_sort(cd.begin(), cd.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
         rdct_status st = ensure_tables(s, (int32_t)jd.size(), (int32_t)cd.size());
         if (st) return st;
         std::memcpy(s.h_jobs, jd.data(), jd.size() * sizeof(JobDesc));
@@ -216,7 +216,7 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         int32_t begin = 0;
         for (int c = 0; c < kBatchGroups; ++c) {
             int32_t end = begin;
-            while (end < (int32_t)cd.size() && cd[end].diag == c) ++end;
+            while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
             if (end > begin)
                 RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2, p->comp));
             begin = end;

@@ -10,8 +10,8 @@
 //      it is admitted, so copies overlap kernels already running;
 //   3. whenever one of the compute streams is free, launches every admitted,
 //      copied request (up to max_batch) as one batch: one persistent kernel
-//      per anti-diagonal class of r over a flattened strip index, then the
-//      device->host copies of the reconstructions and per-image errors;
+//      per r present over a flattened strip index, then the device->host
+//      copies of the reconstructions and per-image errors;
 //   4. polls completion events, finishes results, frees buffers and wakes
 //      waiters.
 // Requests that arrive while launches are in flight join the next launch
@@ -168,14 +168,14 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
             uint8_t *dst = r.q.dst ? base + (r.q.planes + p) * plane : nullptr;
             JobDesc d = make_job(pl, dst, r.q.w, nullptr, 0, r.q.r, i, 1);
             const int items = strips_of(d, kFusedVRows);
-            const int diag = diag_class_host(r.q.r);
+            const int cls = fused_class_of(r.q.r, 2);
             for (int it = 0; it < items; it += kServerItemsPerChunk)
-                chunks.push_back(Chunk{(int32_t)jobs.size(), it, std::min(kServerItemsPerChunk, items - it), diag});
+                chunks.push_back(Chunk{(int32_t)jobs.size(), it, std::min(kServerItemsPerChunk, items - it), cls});
             jobs.push_back(d);
         }
         RDCT_CUDA_TRY(cudaStreamWaitEvent(L.s, r.copied, 0));
     }
-    std::stable_sort(chunks.begin(), chunks.end(), [](const Chunk &a, const Chunk &b) { return a.diag < b.diag; });
+    std::stable_sort(chunks.begin(), chunks.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
     if (!grow(L, (int32_t)jobs.size(), (int32_t)chunks.size(), n))
         return set_error(RDCT_ERR_OOM, "rdct_server: table allocation failed");
     std::memcpy(L.h_jobs, jobs.data(), jobs.size() * sizeof(JobDesc));
@@ -186,9 +186,9 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
     int32_t begin = 0;
     while (begin < (int32_t)chunks.size()) {
         int32_t end = begin;
-        while (end < (int32_t)chunks.size() && chunks[end].diag == chunks[begin].diag) ++end;
+        while (end < (int32_t)chunks.size() && chunks[end].cls == chunks[begin].cls) ++end;
         RDCT_CUDA_TRY(
-            launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, chunks[begin].diag, 0, 4, 2, L.s));
+            launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, chunks[begin].cls, 0, 4, 2, L.s));
         begin = end;
     }
     for (int32_t i = 0; i < n; ++i) {
