@@ -291,6 +291,18 @@ RDCT_API rdct_status rdct_pipeline_run(rdct_pipeline *pipe, const rdct_host_job 
                               double *sse_per_image);
 RDCT_API rdct_status rdct_pipeline_destroy(rdct_pipeline *pipe);
 
+/* How rdct_pipeline_run moves the planes:
+ *   AUTO (default)  DIRECT when every plane (src and dst) is pinned host
+ *                   memory the device addresses with the same pointer, else
+ *                   STAGED;
+ *   STAGED          host->device copies into device slots, kernels on the
+ *                   slots, device->host copies, overlapped on three streams;
+ *   DIRECT          the fused kernels read and write the host planes over the
+ *                   host link (no staging); RDCT_ERR_ARG if a plane is not
+ *                   pinned. */
+enum { RDCT_PIPELINE_AUTO = 0, RDCT_PIPELINE_STAGED = 1, RDCT_PIPELINE_DIRECT = 2 };
+RDCT_API rdct_status rdct_pipeline_set_mode(rdct_pipeline *pipe, int32_t mode);
+
 /* ----------------------------------------------------------------- serving */
 
 typedef struct {

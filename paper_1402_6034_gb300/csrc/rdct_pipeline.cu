@@ -1,7 +1,10 @@
 // rdct_pipeline.cu -- planes that live in host memory, streamed through the
 // fused path with copies and kernels overlapped.
 //
-// Planes are cut into horizontal bands (whole block rows; 8x8 blocks are
+// Direct mode (pinned host planes): the fused kernels load and store the
+// planes in host memory themselves, over the host link, and nothing is
+// staged.  Staged mode (any host memory):
+// planes are cut into horizontal bands (whole block rows; 8x8 blocks are
 // independent, Sec. 3), bands are packed into groups that fit one staging
 // slot, and each group goes host->device on one stream, through one batch
 // launch on a second, and device->host on a third.  `depth` slots rotate so
@@ -43,6 +46,7 @@ constexpr int kItemsPerChunk = 8;
 
 struct rdct_pipeline {
     int device = 0;
+    int mode = RDCT_PIPELINE_AUTO;
     int64_t slot_bytes = 0;  // per direction
     std::vector<Slot> slots;
     cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
@@ -99,7 +103,82 @@ static rdct_status ensure_tables(Slot &s, int32_t njobs, int32_t nchunks) {
     return RDCT_OK;
 }
 
+// True when the device can address [p, p + bytes) with the same pointer:
+// pinned (page-locked) host memory under unified addressing.  The first and
+// the last byte are checked; a plane is one user buffer, so both ends being
+// pinned means the buffer was pinned as a whole.
+static bool device_addressable(const void *p, int64_t bytes) {
+    const void *ends[2] = {p, static_cast<const uint8_t *>(p) + (bytes > 0 ? bytes - 1 : 0)};
+    for (const void *q : ends) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer != q) return false;
+    }
+    return true;
+}
+
+// Direct mode: the fused kernels read the planes from host memory and write
+// the reconstructions back to host memory over the host link, with no
+// staging copies; only the job and chunk tables and the per-image errors
+// cross the link as copies.
+static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32_t njobs) {
+    std::vector<JobDesc> jd;
+    std::vector<Chunk> cd;
+    jd.reserve(njobs);
+    for (int32_t i = 0; i < njobs; ++i) {
+        const rdct_host_job &j = jobs[i];
+        rdct_plane pl{j.src, j.pitch, j.w, j.h};
+        JobDesc d = make_job(pl, j.dst, j.pitch, nullptr, 0, j.r, j.image, 1);
+        const int items = strips_of(d, kFusedVRows);
+        const int cls = fused_class_of(j.r, 2);
+        for (int it = 0; it < items; it += kItemsPerChunk)
+            cd.push_back(Chunk{i, it, std::min(kItemsPerChunk, items - it), cls});
+        jd.push_back(d);
+    }
+    std::stable_sort(cd.begin(), cd.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
+    Slot &s = p->slots[0];
+    rdct_status st = ensure_tables(s, (int32_t)jd.size(), (int32_t)cd.size());
+    if (st) return st;
+    std::memcpy(s.h_jobs, jd.data(), jd.size() * sizeof(JobDesc));
+    std::memcpy(s.h_chunks, cd.data(), cd.size() * sizeof(Chunk));
+    RDCT_CUDA_TRY(cudaMemcpyAsync(s.d_jobs, s.h_jobs, jd.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, p->comp));
+    RDCT_CUDA_TRY(cudaMemcpyAsync(s.d_chunks, s.h_chunks, cd.size() * sizeof(Chunk), cudaMemcpyHostToDevice, p->comp));
+    int32_t begin = 0;
+    for (int c = 0; c < kBatchGroups; ++c) {
+        int32_t end = begin;
+        while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
+        if (end > begin)
+            RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2, p->comp));
+        begin = end;
+    }
+    return RDCT_OK;
+}
+
+// Wait for the run and hand the per-image errors to the host.
+static rdct_status finish_run(rdct_pipeline *p, int32_t nimages, double *sse_per_image) {
+    RDCT_CUDA_TRY(cudaStreamSynchronize(p->comp));
+    RDCT_CUDA_TRY(cudaStreamSynchronize(p->d2h));
+    if (nimages > 0) {
+        std::vector<unsigned long long> acc(nimages);
+        RDCT_CUDA_TRY(cudaMemcpy(acc.data(), p->d_acc, (size_t)nimages * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < nimages; ++i) sse_per_image[i] = (double)acc[i] / 576.0;
+    }
+    return RDCT_OK;
+}
+
 extern "C" {
+
+rdct_status rdct_pipeline_set_mode(rdct_pipeline *p, int32_t mode) {
+    if (!p) return set_error(RDCT_ERR_ARG, "rdct_pipeline_set_mode: null pipeline");
+    if (mode != RDCT_PIPELINE_AUTO && mode != RDCT_PIPELINE_STAGED && mode != RDCT_PIPELINE_DIRECT)
+        return set_error(RDCT_ERR_ARG, "rdct_pipeline_set_mode: unknown mode");
+    p->mode = mode;
+    return RDCT_OK;
+}
 
 rdct_status rdct_pipeline_create(int64_t device_budget_bytes, int32_t depth, rdct_pipeline **pipe) {
     if (!pipe) return set_error(RDCT_ERR_ARG, "rdct_pipeline_create: null result");
@@ -154,6 +233,20 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         p->acc_cap = nimages;
     }
     if (nimages > 0) RDCT_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, (size_t)nimages * sizeof(unsigned long long), p->comp));
+
+    bool direct = p->mode != RDCT_PIPELINE_STAGED;
+    for (int32_t i = 0; i < njobs && direct; ++i) {
+        const rdct_host_job &j = jobs[i];
+        const int64_t bytes = (int64_t)(j.h - 1) * j.pitch + j.w;
+        direct = device_addressable(j.src, bytes) && (!j.dst || device_addressable(j.dst, bytes));
+    }
+    if (p->mode == RDCT_PIPELINE_DIRECT && !direct)
+        return set_error(RDCT_ERR_ARG, "rdct_pipeline_run: direct mode needs pinned host planes");
+    if (direct) {
+        rdct_status st = run_direct(p, jobs, njobs);
+        if (st) return st;
+        return finish_run(p, nimages, sse_per_image);
+    }
 
     // cut planes into bands that fit a slot, packed 256-byte aligned, tight pitch = w
     std::vector<std::vector<Band>> groups(1);
@@ -232,16 +325,7 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         RDCT_CUDA_TRY(cudaEventRecord(s.out_done, p->d2h));
         s.used = true;
     }
-    // results
-    RDCT_CUDA_TRY(cudaStreamSynchronize(p->comp));
-    RDCT_CUDA_TRY(cudaStreamSynchronize(p->d2h));
-    if (nimages > 0) {
-        std::vector<unsigned long long> acc(nimages);
-        RDCT_CUDA_TRY(cudaMemcpy(acc.data(), p->d_acc, (size_t)nimages * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost));
-        for (int32_t i = 0; i < nimages; ++i) sse_per_image[i] = (double)acc[i] / 576.0;
-    }
-    return RDCT_OK;
+    return finish_run(p, nimages, sse_per_image);
 }
 
 rdct_status rdct_pipeline_destroy(rdct_pipeline *p) {

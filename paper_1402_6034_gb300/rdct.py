@@ -101,6 +101,7 @@ _SIGS = {
     "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_uqi": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp],
     "rdct_variant_matrices": [ctypes.c_int, _vp, _vp],
+    "rdct_pipeline_set_mode": [_vp, _i32],
     "rdct_spectral_error": [ctypes.c_int, _i32, _vp, _vp],
     "rdct_fused_variant": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
@@ -432,10 +433,13 @@ def autotune(jobs: list[BatchJob], nimages: int, stream=None) -> dict:
 class Pipeline:
     """Planes in host memory streamed through the fused path (copies overlapped with kernels)."""
 
-    def __init__(self, device_budget_bytes: int = 1 << 30, depth: int = 3):
+    AUTO, STAGED, DIRECT = 0, 1, 2
+
+    def __init__(self, device_budget_bytes: int = 1 << 30, depth: int = 3, mode: int = 0):
         h = ctypes.c_void_p()
         _check(load().rdct_pipeline_create(device_budget_bytes, depth, ctypes.byref(h)), "rdct_pipeline_create")
         self._h = h
+        _check(load().rdct_pipeline_set_mode(h, mode), "rdct_pipeline_set_mode")
 
     def run(self, jobs: list[tuple], nimages: int):
         """jobs: (src, dst or None, r, image) with src/dst 2-D uint8 host arrays (numpy or CPU tensors)."""

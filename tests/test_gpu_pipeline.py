@@ -1,0 +1,93 @@
+"""The host pipeline (rdct_pipeline_run): planes in host memory, staged through device slots
+(copies overlapped with kernels) or read and written in place by the kernels (direct mode,
+pinned memory).  Both must give exactly what the device-resident path gives: the same uint8
+reconstruction and the same per-image error (576 * SSE is an exact integer on every route);
+a few planes are also checked against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1402_6034_gb300 import rdct, synth
+from tests.gpu_helpers import assert_u8_close, cuda_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    d = cuda_or_skip()
+    rdct.load()
+    return d
+
+
+def _planes(seed, pinned):
+    """Mixed sizes, padded pitches, r per image; images 0..3 with 1-3 planes each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = [(0, 264, 1000, 16), (0, 136, 72, 16), (1, 1080, 1920, 4), (2, 8, 8, 64), (2, 520, 512, 1),
+             (3, 2160, 3840, 32), (3, 1080, 1920, 32), (3, 1080, 1920, 32)]
+    out = []
+    for k, (img, h, w, r) in enumerate(specs):
+        pitch = w + (0 if k % 2 else 40)
+        a = synth.image_1f(h, w, seed=seed * 100 + k) if k != 3 else rng.integers(0, 256, (h, w), dtype=np.uint8)
+        src = torch.zeros((h, pitch), dtype=torch.uint8)
+        src[:, :w] = torch.from_numpy(np.ascontiguousarray(a))
+        dst = torch.full((h, pitch), 7, dtype=torch.uint8)
+        if pinned:
+            src, dst = src.pin_memory(), dst.pin_memory()
+        out.append((src[:, :w], dst[:, :w], r, img))
+    return out
+
+
+def _device_reference(jobs, dev):
+    outs, sse = [], np.zeros(4)
+    for src, _, r, img in jobs:
+        u8, _, s = rdct.fused(src.contiguous().to(dev), r)
+        outs.append(u8.cpu())
+        sse[img] += s.item()
+    return outs, sse
+
+
+@pytest.mark.parametrize("mode,pinned", [(rdct.Pipeline.STAGED, False), (rdct.Pipeline.STAGED, True),
+                                         (rdct.Pipeline.DIRECT, True), (rdct.Pipeline.AUTO, True),
+                                         (rdct.Pipeline.AUTO, False)])
+def test_pipeline_matches_device_path(dev, mode, pinned):
+    jobs = _planes(1, pinned)
+    ref_out, ref_sse = _device_reference(jobs, dev)
+    # a small budget: 3 slots of about 2.7 MB force bands and several groups
+    p = rdct.Pipeline(device_budget_bytes=8 << 20, depth=3, mode=mode)
+    sse = p.run(jobs, 4)
+    p.close()
+    for (src, dst, r, img), ref in zip(jobs, ref_out):
+        assert torch.equal(dst, ref), (src.shape, r)
+    np.testing.assert_allclose(sse, ref_sse, rtol=1e-12, atol=1e-9)
+    # the padding after each row is untouched
+    for src, dst, r, img in jobs:
+        full = dst.as_strided((dst.shape[0], dst.stride(0)), (dst.stride(0), 1))
+        if full.shape[1] > dst.shape[1]:
+            assert bool((full[:, dst.shape[1]:] == 7).all())
+
+
+def test_pipeline_against_oracle(dev):
+    jobs = _planes(2, True)
+    p = rdct.Pipeline(device_budget_bytes=64 << 20, depth=2, mode=rdct.Pipeline.DIRECT)
+    sse = p.run(jobs, 4)
+    p.close()
+    tot = np.zeros(4)
+    for src, dst, r, img in jobs[:5]:
+        xo, uo, so, _ = orc.fused(np.ascontiguousarray(src.numpy()), r)
+        assert_u8_close(dst.numpy(), uo, xo, tie_window=1e-6)
+        tot[img] += so
+    for img in (0, 1, 2):
+        assert sse[img] == pytest.approx(tot[img], rel=1e-9, abs=1e-9)
+
+
+def test_pipeline_sse_only_and_direct_refuses_pageable(dev):
+    jobs = [(src, None, r, img) for src, _, r, img in _planes(3, True)]
+    ref = _device_reference(jobs, dev)[1]
+    p = rdct.Pipeline(device_budget_bytes=32 << 20, depth=2, mode=rdct.Pipeline.DIRECT)
+    np.testing.assert_allclose(p.run(jobs, 4), ref, rtol=1e-12, atol=1e-9)
+    pageable = [(torch.from_numpy(src.numpy().copy()), None, r, img) for src, _, r, img in jobs]
+    with pytest.raises(rdct.RdctError):
+        p.run(pageable, 4)
+    p.close()
