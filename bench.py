@@ -268,6 +268,30 @@ def cpu_oracle_rate(planes_iter, r: int, budget_s: float):
 
 # ------------------------------------------------------- uneven / sweep modes
 
+def host_link_rate(dev, nbytes: int = 1 << 30, reps: int = 5) -> float:
+    """GB/s each way of plain pinned-host <-> device copies running at the same time on two streams: the
+    ceiling for any end-to-end path that moves every input in and every output out."""
+    hin = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    hout = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    din = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dout = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def both():
+        with torch.cuda.stream(s1):
+            din.copy_(hin, non_blocking=True)
+        with torch.cuda.stream(s2):
+            hout.copy_(dout, non_blocking=True)
+
+    both()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        both()
+    torch.cuda.synchronize()
+    return nbytes / ((time.perf_counter() - t) / reps) / 1e9
+
+
 def events_time(fn, steps, warmup, stream):
     for _ in range(warmup):
         fn()
@@ -649,11 +673,13 @@ def main():
 
         dt, ok = time_pipeline(rdct.Pipeline.AUTO)
         dt_s, ok_s = time_pipeline(rdct.Pipeline.STAGED)
+        link = host_link_rate(dev)
         line["e2e"] = {"value": world * wl.samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": wl.samples,
                        "d2h_bytes_per_step": wl.samples + 8 * wl.nimages, "ms_per_step": 1000 * dt,
                        "api": "rdct_pipeline_run on pinned host planes, direct mode: the fused kernels read and "
                               "write the host planes over the host link (no staging copies)",
                        "sse_matches_device_path": ok,
+                       "host_link_GBs_each_way": link,
                        "staged": {"value": world * wl.samples / dt_s / 1e9, "ms_per_step": 1000 * dt_s,
                                   "api": "rdct_pipeline_run, staged mode: copies into device slots overlapped "
                                          "with kernels on three streams", "sse_matches_device_path": ok_s}}
