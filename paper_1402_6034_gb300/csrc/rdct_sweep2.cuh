@@ -24,18 +24,15 @@ namespace rdct {
 // most 16320^2 < 2^28 to a bin, so 16 blocks fit.
 static_assert(kSweepChunkStrips * kFusedVRows * 16320ull * 16320ull < (1ull << 32), "sweep bins overflow");
 
+// One output column at a time: column j of C0 A (the row pass, two dp4a per
+// row on the packed pixels), then the column butterfly, then its eight
+// energies; only eight intermediates are live next to the 64 bins.
 __device__ __forceinline__ void sweep_rdct_block(const uint2 (&w)[8], unsigned (&bins)[64]) {
-    int R[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            R[i][k] = dp4a_us(w[i].x, c0_row_word(k, 0), dp4a_us(w[i].y, c0_row_word(k, 1), 0));
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int c[8], o[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
+        for (int i = 0; i < 8; ++i) c[i] = dp4a_us(w[i].x, c0_row_word(j, 0), dp4a_us(w[i].y, c0_row_word(j, 1), 0));
         c0_forward(c, o);
 #pragma unroll
         for (int i = 0; i < 8; ++i) bins[i * 8 + j] += (unsigned)(o[i] * o[i]);
@@ -93,7 +90,8 @@ __device__ __forceinline__ void sweep_flush(double *plane_bins, unsigned (&ub)[6
 // Persistent sweep kernel over a chunk table (job = plane; out = [planes][64]
 // zigzag-ordered bins: uint64 576-scaled energies for RDCT, double for DCT).
 template <int KIND>
-__global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, double *out, const DctConsts C) {
+__global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_kernel(const Fused2Args a, double *out,
+                                                                                   const DctConsts C) {
     constexpr int THREADS = 128;
     __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
     const int lane = threadIdx.x & 31;
@@ -131,7 +129,9 @@ __global__ void __launch_bounds__(128, 3) sweep2_kernel(const Fused2Args a, doub
         } else {
             cp_async_commit();
         }
-#pragma unroll 1
+        // RDCT: both blocks unrolled so that their work interleaves; DCT: one
+        // after the other (its FP32 intermediates leave no registers to spare)
+#pragma unroll (KIND == RDCT_KIND_RDCT ? kVRows : 1)
         for (int v = 0; v < kVRows; ++v) {
             if (v < nblk) {
                 uint2 w[8];
