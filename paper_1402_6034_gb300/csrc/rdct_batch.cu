@@ -103,11 +103,13 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
 cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
+    bool first = true;
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
         if (n == 0) continue;
         e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm, p->tune.warps_per_cta,
-                               p->tune.blocks_per_thread, s);
+                               p->tune.blocks_per_thread, !first, s);
+        first = false;
     }
     if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
     return e;

@@ -390,9 +390,11 @@ inline void launch_persistent(K kernel, int64_t units, int ctas_per_sm, int warp
 // the smallest size that holds them, so the rest of the SM's 256 KB stays L1
 // (the copies into the ring are cached in L1; a larger carve-out measurably
 // slows them down).
+// overlap: launch as a programmatic dependent of the previous kernel in the
+// stream (the kernel must trigger and wait with griddepcontrol itself).
 template <typename K, typename... Args>
-inline void launch_staged(K kernel, int64_t units, int ctas_per_sm, int warps, int max_ctas, int smem_per_cta,
-                          cudaStream_t s, Args... args) {
+inline cudaError_t launch_staged(K kernel, int64_t units, int ctas_per_sm, int warps, int max_ctas, int smem_per_cta,
+                                 bool overlap, cudaStream_t s, Args... args) {
     const int threads = warps * 32;
     int per_sm = resident_ctas(kernel, threads);
     if (per_sm > max_ctas) per_sm = max_ctas;
@@ -402,7 +404,17 @@ inline void launch_staged(K kernel, int64_t units, int ctas_per_sm, int warps, i
     int64_t g = (int64_t)sm_count() * per_sm;
     const int64_t need = (units + warps - 1) / warps;
     if (g > need) g = need;
-    kernel<<<(int)(g < 1 ? 1 : g), threads, 0, s>>>(args...);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(g < 1 ? 1 : g));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = overlap ? attr : nullptr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // Single-plane fused launch for one output mode and transform kind; the

@@ -41,9 +41,11 @@ int batch_group_of_class(int cls, int blocks_per_thread) {
 }
 
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
-                               int group, int ctas_per_sm, int warps, int blocks_per_thread, cudaStream_t s) {
+                               int group, int ctas_per_sm, int warps, int blocks_per_thread, bool overlap,
+                               cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
-    if (blocks_per_thread == 2) return launch_fused2_batch(jobs, chunks, nchunks, acc_u64, group + 1, ctas_per_sm, s);
+    if (blocks_per_thread == 2)
+        return launch_fused2_batch(jobs, chunks, nchunks, acc_u64, group + 1, ctas_per_sm, overlap, s);
     if (group == 0) launch_persistent(fused_batch_kernel<1, 0, 5>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
     else if (group == 1) launch_persistent(fused_batch_kernel<1, 6, 8>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);
     else launch_persistent(fused_batch_kernel<1, 9, 14>, nchunks, ctas_per_sm, warps, s, jobs, chunks, nchunks, acc_u64);

@@ -342,6 +342,10 @@ __device__ __forceinline__ void fetch_strip(const JobDesc &job, int rp, int bx, 
 template <int CLO, int CHI, bool SINGLE, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args a) {
     __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
+    // The next launch of a batch (another r) may start as CTAs of this one
+    // retire: the launches touch disjoint planes and only add into the error
+    // slots.  Without a programmatic dependent launch this is a no-op.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -401,20 +405,24 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
         }
     }
     cp_async_wait<0>();
+    // Complete only after the launch this one overlapped has completed, so
+    // that whatever follows the last launch of a batch in stream order sees
+    // every launch's errors.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Launch for exactly r = R retained coefficients: single-plane (a.single) or
 // batch (a.jobs / a.chunks).  Instantiated per R in rdct_fused2_r*.cu.
+// overlap: a programmatic dependent launch on the previous kernel of the
+// stream (batch launches after the first of a batch).
 template <int R>
-cudaError_t launch_fused2_r(const Fused2Args &a, bool single, int ctas_per_sm, cudaStream_t s) {
+cudaError_t launch_fused2_r(const Fused2Args &a, bool single, int ctas_per_sm, bool overlap, cudaStream_t s) {
     constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
     if (single)
-        launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
-                      kFused2Smem, s, a);
-    else
-        launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
-                      kFused2Smem, s, a);
-    return cudaGetLastError();
+        return launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB>, a.nchunks, ctas_per_sm, T / 32,
+                             kFused2MaxCtas, kFused2Smem, false, s, a);
+    return launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+                         kFused2Smem, overlap, s, a);
 }
 
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<1>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<2>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<3>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<4>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<5>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<6>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<7>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<8>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<1>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<2>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<3>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<4>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<5>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<6>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<7>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<8>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<9>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<10>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<11>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<12>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<13>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<14>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<15>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<16>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<9>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<10>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<11>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<12>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<13>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<14>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<15>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<16>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<17>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<18>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<19>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<20>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<21>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<22>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<23>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<24>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<17>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<18>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<19>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<20>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<21>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<22>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<23>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<24>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

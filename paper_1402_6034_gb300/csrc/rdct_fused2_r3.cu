@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<25>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<26>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<27>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<28>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<29>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<30>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<31>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<32>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<25>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<26>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<27>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<28>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<29>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<30>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<31>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<32>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<33>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<34>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<35>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<36>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<37>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<38>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<39>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<40>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<33>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<34>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<35>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<36>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<37>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<38>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<39>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<40>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<41>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<42>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<43>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<44>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<45>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<46>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<47>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<48>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<41>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<42>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<43>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<44>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<45>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<46>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<47>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<48>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

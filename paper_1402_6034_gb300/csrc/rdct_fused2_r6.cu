@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<49>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<50>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<51>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<52>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<53>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<54>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<55>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<56>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<49>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<50>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<51>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<52>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<53>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<54>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<55>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<56>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -3,12 +3,12 @@
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<57>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<58>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<59>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<60>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<61>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<62>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<63>(const Fused2Args &, bool, int, cudaStream_t);
-template cudaError_t launch_fused2_r<64>(const Fused2Args &, bool, int, cudaStream_t);
+template cudaError_t launch_fused2_r<57>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<58>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<59>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<60>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<61>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<62>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<63>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<64>(const Fused2Args &, bool, int, bool, cudaStream_t);
 }  // namespace rdct

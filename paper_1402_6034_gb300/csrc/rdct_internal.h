@@ -105,14 +105,18 @@ int fused_class_of(int r, int blocks_per_thread);
 int batch_group_of_class(int cls, int blocks_per_thread);
 // blocks_per_thread 2 selects the dp4a/f32x2 kernel (128 threads per CTA,
 // strips of kFusedVRows block rows), 1 the scalar kernel with `warps` warps.
+// overlap (blocks_per_thread 2): the launch may start while the previous
+// launch of the same batch in the stream drains (programmatic dependent
+// launch); pass false for the first launch of a batch.
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
-                               int group, int ctas_per_sm, int warps, int blocks_per_thread, cudaStream_t s);
+                               int group, int ctas_per_sm, int warps, int blocks_per_thread, bool overlap,
+                               cudaStream_t s);
 // The fused kernel for sm_103a issue rates (dp4a row pass, f32x2 inverse,
 // cp.async ring): uint8 output or error only, any alignment.
 cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, int ctas_per_sm, int chunk_items,
                                  cudaStream_t s);
 cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
-                                int r, int ctas_per_sm, cudaStream_t s);
+                                int r, int ctas_per_sm, bool overlap, cudaStream_t s);
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are

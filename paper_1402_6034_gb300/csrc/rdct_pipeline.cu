@@ -150,8 +150,10 @@ static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32
     for (int c = 0; c < kBatchGroups; ++c) {
         int32_t end = begin;
         while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
-        if (end > begin)
-            RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2, p->comp));
+        if (end > begin) {
+            RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2,
+                                             begin > 0, p->comp));
+        }
         begin = end;
     }
     return RDCT_OK;
@@ -310,8 +312,10 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         for (int c = 0; c < kBatchGroups; ++c) {
             int32_t end = begin;
             while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
-            if (end > begin)
-                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2, p->comp));
+            if (end > begin) {
+                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2,
+                                                 begin > 0, p->comp));
+            }
             begin = end;
         }
         RDCT_CUDA_TRY(cudaEventRecord(s.computed, p->comp));

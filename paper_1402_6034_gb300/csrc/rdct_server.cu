@@ -187,8 +187,8 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
     while (begin < (int32_t)chunks.size()) {
         int32_t end = begin;
         while (end < (int32_t)chunks.size() && chunks[end].cls == chunks[begin].cls) ++end;
-        RDCT_CUDA_TRY(
-            launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, chunks[begin].cls, 0, 4, 2, L.s));
+        RDCT_CUDA_TRY(launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, chunks[begin].cls, 0, 4,
+                                         2, begin > 0, L.s));
         begin = end;
     }
     for (int32_t i = 0; i < n; ++i) {

@@ -14,11 +14,10 @@ cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchu
     a.chunks = chunks;
     a.nchunks = nchunks;
     if (kind == RDCT_KIND_RDCT)
-        launch_staged(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, s, a, out, DctConsts{});
-    else
-        launch_staged(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, s, a, out,
-                      make_dct_consts());
-    return cudaGetLastError();
+        return launch_staged(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, false, s, a,
+                             out, DctConsts{});
+    return launch_staged(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, false, s, a, out,
+                         make_dct_consts());
 }
 
 namespace {
