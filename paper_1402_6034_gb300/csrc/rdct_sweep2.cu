@@ -30,47 +30,37 @@ __device__ int align_class(const void *p, int64_t pitch) {
 }
 
 // Up to kSweepBuildBatch planes, passed by value so that building the tables
-// needs no host-to-device copy (and no stream synchronisation).
+// needs no host-to-device copy (and no stream synchronisation); cbase[i] is
+// the index of plane i's first chunk (a host prefix sum).
 struct PlaneBatch {
     rdct_plane p[kSweepBuildBatch];
-    int32_t first, n, chunk_base;
+    int32_t cbase[kSweepBuildBatch];
+    int32_t first, n;
 };
 
-// One CTA: a job descriptor per plane and the chunks (runs of at most
-// kSweepChunkStrips items of 32 column pairs) of this batch, starting at
-// chunk index chunk_base.
-__global__ void __launch_bounds__(1024) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks) {
-    __shared__ int32_t s_cnt[kSweepBuildBatch + 1];
-    const int i = threadIdx.x;
-    int32_t items = 0;
-    if (i < b.n) {
-        const rdct_plane pl = b.p[i];
-        JobDesc j{};
-        j.src = pl.ptr;
-        j.src_pitch = pl.pitch;
-        j.nbw = pl.w / 8;
-        j.nbh = pl.h / 8;
-        j.r = 64;
-        j.image = b.first + i;
-        j.segs = (j.nbw + 31) / 32;
-        j.align = align_class(pl.ptr, pl.pitch);
-        j.dalign = 16;
-        jobs[b.first + i] = j;
-        items = fused_items_of(j);
-    }
-    s_cnt[i + 1] = (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
-    __syncthreads();
-    // inclusive scan of the chunk counts (Hillis-Steele over the CTA)
-    for (int off = 1; off < kSweepBuildBatch; off <<= 1) {
-        const int32_t v = (i + 1 - off >= 1) ? s_cnt[i + 1 - off] : 0;
-        __syncthreads();
-        s_cnt[i + 1] += v;
-        __syncthreads();
-    }
-    if (i < b.n) {
-        int32_t c = b.chunk_base + (i == 0 ? 0 : s_cnt[i]);
-        for (int32_t it = 0; it < items; it += kSweepChunkStrips, ++c)
-            chunks[c] = Chunk{b.first + i, it, items - it < kSweepChunkStrips ? items - it : kSweepChunkStrips, 0};
+// One warp per plane: every lane reads the same descriptor (a broadcast from
+// the parameter bank), lane 0 writes the job, and the lanes write the plane's
+// chunks (runs of at most kSweepChunkStrips items of 32 column pairs).
+__global__ void __launch_bounds__(32) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks) {
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x;
+    const rdct_plane pl = b.p[i];
+    JobDesc j{};
+    j.src = pl.ptr;
+    j.src_pitch = pl.pitch;
+    j.nbw = pl.w / 8;
+    j.nbh = pl.h / 8;
+    j.r = 64;
+    j.image = b.first + i;
+    j.segs = (j.nbw + 31) / 32;
+    j.align = align_class(pl.ptr, pl.pitch);
+    j.dalign = 16;
+    if (lane == 0) jobs[b.first + i] = j;
+    const int32_t items = fused_items_of(j);
+    const int32_t nch = (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
+    for (int32_t t = lane; t < nch; t += 32) {
+        const int32_t it = t * kSweepChunkStrips;
+        chunks[b.cbase[i] + t] = Chunk{b.first + i, it, items - it < kSweepChunkStrips ? items - it : kSweepChunkStrips, 0};
     }
 }
 
@@ -88,12 +78,12 @@ cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *job
         PlaneBatch b;
         b.first = first;
         b.n = std::min(kSweepBuildBatch, n - first);
-        b.chunk_base = base;
         for (int32_t i = 0; i < b.n; ++i) {
             b.p[i] = planes[first + i];
+            b.cbase[i] = base;
             base += (int32_t)sweep_chunk_count(planes[first + i]);
         }
-        build_sweep_tables_kernel<<<1, kSweepBuildBatch, 0, s>>>(b, jobs, chunks);
+        build_sweep_tables_kernel<<<b.n, 32, 0, s>>>(b, jobs, chunks);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -39,6 +39,63 @@ __device__ __forceinline__ void sweep_rdct_block(const uint2 (&w)[8], unsigned (
     }
 }
 
+// 8-point orthonormal DCT of an f32x2 pair of vectors (even/odd split, FMAs
+// with the FP32 cos constants, each constant used for both halves).
+__device__ __forceinline__ void dct8_f2(const f2 (&x)[8], f2 (&X)[8], const DctConsts &C) {
+    f2 a[4], b[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        a[n] = x[n] + x[7 - n];
+        b[n] = x[n] - x[7 - n];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const f2(&v)[4] = (k & 1) ? b : a;
+        f2 acc = mul2(f2_make(C.c[k * 8], C.c[k * 8]), v[0]);
+#pragma unroll
+        for (int n = 1; n < 4; ++n) acc = fma2(f2_make(C.c[k * 8 + n], C.c[k * 8 + n]), v[n], acc);
+        X[k] = acc;
+    }
+}
+
+// Exact DCT energies of one block with f32x2 arithmetic: the row pass runs on
+// pairs of rows, the column pass on pairs of columns.  Pixels become floats
+// by placing each byte under the exponent of 2^23 (a byte permute) and
+// subtracting 2^23, exactly.
+__device__ __forceinline__ void sweep_dct_block2(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
+    const f2 two23 = f2_make(8388608.0f, 8388608.0f);
+    float R[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+        f2 x[8], X[8];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const unsigned sel = 0x7540u + (unsigned)n;
+            x[n] = f2_make(__int_as_float((int)__byte_perm(w[i].x, 0x4B000000u, sel)),
+                           __int_as_float((int)__byte_perm(w[i + 1].x, 0x4B000000u, sel))) - two23;
+            x[n + 4] = f2_make(__int_as_float((int)__byte_perm(w[i].y, 0x4B000000u, sel)),
+                               __int_as_float((int)__byte_perm(w[i + 1].y, 0x4B000000u, sel))) - two23;
+        }
+        dct8_f2(x, X, C);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) f2_split(X[k], R[i][k], R[i + 1][k]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        f2 c[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = f2_make(R[i][j], R[i][j + 1]);
+        dct8_f2(c, o, C);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float y0, y1;
+            f2_split(o[i], y0, y1);
+            bins[i * 8 + j] = __fmaf_rn(y0, y0, bins[i * 8 + j]);
+            bins[i * 8 + j + 1] = __fmaf_rn(y1, y1, bins[i * 8 + j + 1]);
+        }
+    }
+}
+
 __device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
     float R[8][8];
 #pragma unroll
@@ -138,7 +195,7 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
 #pragma unroll
                 for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
                 if constexpr (KIND == RDCT_KIND_RDCT) sweep_rdct_block(w, ub);
-                else sweep_dct_block(w, fb, C);
+                else sweep_dct_block2(w, fb, C);
             }
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
