@@ -33,7 +33,7 @@ UNIT = "Gpixel/s"
 # DRAM bytes (read + write) per sample of the fused kernel, from the ncu capture summarised in
 # profiles/fused_video_40x4k_r16_ncu.md.  Reported only while the kernel sources still hash to
 # the value they had when the counters were taken.
-FUSED_TRAFFIC = {"sources_sha256_16": "f0d944876efefc3b", "bytes_per_sample": 1.8935}
+FUSED_TRAFFIC = {"sources_sha256_16": "d87a2e7d285c4a81", "bytes_per_sample": 1.8934}
 FUSED_SOURCES = ["rdct_fused2.cuh", "rdct_device.cuh", "rdct_blocks.cuh", "rdct_fused2_launch.cu"]
 
 
@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-single", action="store_true", help="skip the single 512 x 512 image latency")
     ap.add_argument("--workload", choices=["video", "batch512", "uneven", "sweep", "variants"], default="video")
     ap.add_argument("--frames", type=int, default=600)
     ap.add_argument("--r", type=int, default=16)
@@ -292,6 +293,27 @@ def host_link_rate(dev, nbytes: int = 1 << 30, reps: int = 5) -> float:
     return nbytes / ((time.perf_counter() - t) / reps) / 1e9
 
 
+def single_image_latency(dev, r: int = 10, reps: int = 200) -> dict:
+    """One 512 x 512 image at r = 10 (L2-resident): rdct_fused (forward, keep r, inverse, uint8 output,
+    exact SSE) back to back on a stream (CUDA events), and one call at a time with a synchronize after each
+    (host wall clock, launch included)."""
+    from paper_1402_6034_gb300 import rdct, synth
+    img = torch.from_numpy(synth.image_1f(512, 512, alpha=2.0, seed=0)).to(dev)
+    out = torch.empty_like(img)
+    sse = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    us = events_time(lambda: rdct.fused(img, r, out_u8=out, sse=sse, stream=stream), reps, 10, stream) * 1e3
+    walls = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        rdct.fused(img, r, out_u8=out, sse=sse, stream=stream)
+        torch.cuda.synchronize()
+        walls.append((time.perf_counter() - t) * 1e6)
+    mse = float(sse.item()) / img.numel()
+    return {"image": "512x512 uint8, r = 10", "device_us_per_call": us,
+            "wall_us_per_call_p50": statistics.median(walls), "psnr_db": 10 * math.log10(255.0 ** 2 / mse)}
+
+
 def events_time(fn, steps, warmup, stream):
     for _ in range(warmup):
         fn()
@@ -338,7 +360,7 @@ def bench_uneven(args, dev):
     psnr = 10 * torch.log10(255.0 ** 2 / (sse_g / npix))
     peak, kind = peaks()
     alg = 2 * total + 8 * n
-    nclass = len({synth_diag(sp.r) for sp in specs})
+    nclass = len({sp.r for sp in specs})  # one kernel per r present
     return {"metric": METRIC, "value": total / (ms_graph / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -353,17 +375,6 @@ def bench_uneven(args, dev):
                                    "launches_per_step": len(jobs) + 1},
             "batched_over_per_plane": ms_plain / ms_graph, "sse_identical": identical,
             "quality": {"mean_psnr_db": float(psnr.mean())}}
-
-
-def synth_diag(r):
-    """Anti-diagonal class of r (the diagonal holding zigzag rank r - 1)."""
-    k, s, before = r - 1, 0, 0
-    while True:
-        ln = s + 1 if s < 8 else 15 - s
-        if k < before + ln:
-            return s
-        before += ln
-        s += 1
 
 
 def bench_sweep(args, dev):
@@ -687,6 +698,8 @@ def main():
 
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(dev, args.serving_requests)
+    if rank == 0 and args.workload == "video" and not args.no_single:
+        line["single_image_512_r10"] = single_image_latency(dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, done, tt = cpu_oracle_rate(wl.cpu_planes(), args.r, args.cpu_seconds)
