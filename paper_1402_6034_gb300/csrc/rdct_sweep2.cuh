@@ -11,8 +11,8 @@
 // RDCT: Y = C0 A C0^T exactly (dp4a row pass on packed pixels, int32 column
 // butterfly); the orthonormal energy of Y_ij is W_ij Y_ij^2 / 576, so the bins
 // hold integer Y^2 sums (exact) and the weights are applied at the flush.
-// DCT: C A C^T in FP32 (even/odd split, FMAs with the cos constants), FP32
-// bins, FP64 plane bins.
+// DCT: C A C^T in FP32 (even/odd split, FMAs with the cos constants, on
+// f32x2 pairs of rows and then of columns), FP32 bins, FP64 plane bins.
 // Staging, strip cursors and chunking are those of the fused kernel.
 #pragma once
 #include "rdct_fused2.cuh"
@@ -62,7 +62,7 @@ __device__ __forceinline__ void dct8_f2(const f2 (&x)[8], f2 (&X)[8], const DctC
 // pairs of rows, the column pass on pairs of columns.  Pixels become floats
 // by placing each byte under the exponent of 2^23 (a byte permute) and
 // subtracting 2^23, exactly.
-__device__ __forceinline__ void sweep_dct_block2(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
+__device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
     const f2 two23 = f2_make(8388608.0f, 8388608.0f);
     float R[8][8];
 #pragma unroll
@@ -93,29 +93,6 @@ __device__ __forceinline__ void sweep_dct_block2(const uint2 (&w)[8], float (&bi
             bins[i * 8 + j] = __fmaf_rn(y0, y0, bins[i * 8 + j]);
             bins[i * 8 + j + 1] = __fmaf_rn(y1, y1, bins[i * 8 + j + 1]);
         }
-    }
-}
-
-__device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
-    float R[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float x[8];
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            x[n] = (float)byte_of(w[i].x, n);
-            x[n + 4] = (float)byte_of(w[i].y, n);
-        }
-        dct_fwd8(x, R[i], C);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float c[8], o[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
-        dct_fwd8(c, o, C);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) bins[i * 8 + j] = __fmaf_rn(o[i], o[i], bins[i * 8 + j]);
     }
 }
 
@@ -195,7 +172,7 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
 #pragma unroll
                 for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
                 if constexpr (KIND == RDCT_KIND_RDCT) sweep_rdct_block(w, ub);
-                else sweep_dct_block2(w, fb, C);
+                else sweep_dct_block(w, fb, C);
             }
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
