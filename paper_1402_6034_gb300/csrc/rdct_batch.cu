@@ -31,6 +31,9 @@ struct rdct_plan {
     int32_t group_begin[kBatchGroups + 1] = {0};  // chunk ranges per launch group
     JobDesc *d_jobs = nullptr;
     Chunk *d_chunks = nullptr;
+    bool tma = false;                // TMA-staged kernel (items: row pair x 32-column segment)
+    std::vector<unsigned char> maps; // one encoded tensor map per job when tma
+    unsigned char *d_maps = nullptr;
     // graph cache: one executable per (sse pointer)
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
@@ -39,6 +42,13 @@ struct rdct_plan {
 };
 
 namespace {
+
+// TMA staging (one box request per warp and item instead of sixteen copies
+// per thread) pays where the kernel is bound by instruction issue: r from 16
+// (anti-diagonal 5) up.  Below, where the kernel runs at the copy bandwidth,
+// the per-thread copies measured faster (their items run on across row ends,
+// so no lane idles at a plane's right edge).
+bool tma_pays(int r) { return diag_class_host(r) >= 5; }
 
 rdct_tune default_tune() {
     rdct_tune t{};
@@ -82,10 +92,16 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
         p->jobs[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, 1);
         p->jobs_pp[i] = p->jobs[i];
     }
+    // TMA staging when every plane allows it and its tensor map encodes (two blocks per thread only)
+    p->tma = p->tune.blocks_per_thread == 2 && njobs > 0 && tma_available();
+    if (p->tma) p->maps.assign((size_t)njobs * kTensorMapBytes, 0);
+    for (int32_t i = 0; i < njobs && p->tma; ++i)
+        p->tma = tma_encode_plane(p->jobs[i], p->maps.data() + (size_t)i * kTensorMapBytes);
+    if (!p->tma) p->maps.clear();
     std::vector<Chunk> ch;
     const int per = p->tune.items_per_chunk;
     for (int32_t i = 0; i < njobs; ++i) {
-        const int items = strips_of(p->jobs[i], vrows);
+        const int items = p->tma && tma_pays(p->jobs[i].r) ? tma_items_of(p->jobs[i]) : strips_of(p->jobs[i], vrows);
         const int c = fused_class_of(p->jobs[i].r, p->tune.blocks_per_thread);
         for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), c});
     }
@@ -107,8 +123,12 @@ cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
     for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
         const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
         if (n == 0) continue;
-        e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm, p->tune.warps_per_cta,
-                               p->tune.blocks_per_thread, !first, s);
+        if (p->tma && tma_pays(g + 1))
+            e = launch_fused2_tma_batch(p->d_jobs, p->d_chunks + b, n, p->d_maps, acc, g + 1, p->tune.ctas_per_sm,
+                                        !first, s);
+        else
+            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm,
+                                   p->tune.warps_per_cta, p->tune.blocks_per_thread, !first, s);
         first = false;
     }
     if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
@@ -174,6 +194,10 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     }
     if (jb) e = cudaMemcpy(p->d_jobs, p->jobs.data(), jb, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && cb) e = cudaMemcpy(p->d_chunks, p->chunks.data(), cb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && p->tma) {
+        e = cudaMalloc(&p->d_maps, p->maps.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_maps, p->maps.data(), p->maps.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
 
     if (e != cudaSuccess) {
@@ -239,6 +263,7 @@ rdct_status rdct_batch_plan_destroy(rdct_plan *p) {
     }
     if (p->d_jobs) cudaFree(p->d_jobs);
     if (p->d_chunks) cudaFree(p->d_chunks);
+    if (p->d_maps) cudaFree(p->d_maps);
     delete p;
     return RDCT_OK;
 }

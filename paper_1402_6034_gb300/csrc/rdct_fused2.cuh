@@ -411,6 +411,156 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// ------------------------------------------------------------ TMA staging
+//
+// Batch plans whose planes all start on 16-byte boundaries with 16-byte
+// pitches stage their pixels with the tensor memory accelerator instead of
+// per-thread copies.  A work item is then one row pair x a segment of 32
+// column pairs starting at a multiple of 32 columns, i.e. one 256 x 16-byte
+// box of the plane, which one lane requests with cp.async.bulk.tensor (the
+// box's columns and rows outside the plane arrive as zeros); each warp has a
+// two-stage ring of boxes and one mbarrier per stage.
+constexpr int kTmaBoxW = 256, kTmaBoxH = 16, kTmaBoxBytes = kTmaBoxW * kTmaBoxH;
+
+struct TmaArgs {
+    const JobDesc *jobs;
+    const Chunk *chunks;        // items: row pair * segments + segment
+    const unsigned char *maps;  // kTensorMapBytes per job
+    int32_t nchunks;
+    unsigned long long *acc;    // per-image 576 * SSE
+};
+
+__device__ unsigned int g_tma_timeouts = 0;
+
+__device__ __forceinline__ bool tma_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// One lane: expect the box's bytes on the stage's mbarrier and request it.
+__device__ __forceinline__ void tma_request(const unsigned char *map, uint32_t dst, uint32_t mbar, int x, int y) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "n"(kTmaBoxBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+template <int CLS, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs a) {
+    constexpr int WARPS = THREADS / 32;
+    __shared__ __align__(128) unsigned char boxes[WARPS * kStages * kTmaBoxBytes];
+    __shared__ __align__(8) unsigned long long bars[WARPS * kStages];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps = (int)(gridDim.x * WARPS);
+    const int gw = (int)(blockIdx.x * WARPS + wid);
+    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(boxes + wid * kStages * kTmaBoxBytes);
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[wid * kStages]);
+    if (lane == 0) {
+#pragma unroll
+        for (int st = 0; st < kStages; ++st) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * st));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
+    // the warp's items, in order: chunks gw, gw + nwarps, ..., each item0 .. item0 + nitems - 1
+    int c = gw, left = 0, item = 0;
+    Chunk ch{};
+    auto load_chunk = [&]() {
+        if (c < a.nchunks) {
+            ch = a.chunks[c];
+            item = ch.item0;
+            left = ch.nitems;
+        }
+    };
+    auto advance = [&]() {
+        if (--left > 0) {
+            ++item;
+        } else {
+            c += nwarps;
+            load_chunk();
+        }
+    };
+    auto request = [&](int st) {  // the current (c, item) into stage st
+        if (lane == 0) {
+            const JobDesc &job = a.jobs[ch.job];
+            const int rp = item / job.segs, seg = item - rp * job.segs;
+            tma_request(a.maps + (int64_t)ch.job * kTensorMapBytes, ring + st * kTmaBoxBytes, bar0 + 8 * st,
+                        seg * kTmaBoxW, rp * kTmaBoxH);
+        }
+    };
+
+    load_chunk();
+    if (c >= a.nchunks) return;
+    request(0);
+    int cur_c = c, citem = item;  // the item in flight in `stage`
+    Chunk cch = ch;
+    advance();                     // (c, item): the next item
+    uint32_t phase = 0u;           // bit st: parity of stage st's next completion
+    unsigned long long s576 = 0;
+    int stage = 0;
+    while (true) {
+        const bool more = c < a.nchunks;
+        if (more) {  // the other stage was read in the previous iteration by every lane
+            __syncwarp();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            request(stage ^ 1);
+        }
+        const bool got = tma_wait(bar0 + 8 * stage, (phase >> stage) & 1u);
+        phase ^= 1u << stage;
+        if (!__all_sync(0xffffffffu, got)) {
+            if (lane == 0) atomicAdd(&g_tma_timeouts, 1u);
+            if (more) tma_wait(bar0 + 8 * (stage ^ 1), (phase >> (stage ^ 1)) & 1u);
+            break;
+        }
+        const JobDesc &job = a.jobs[cch.job];
+        const int rp = citem / job.segs, seg = citem - rp * job.segs;
+        const int bx = seg * 32 + lane, by = 2 * rp;
+        if (bx < job.nbw) {
+            uint2 wa[8], wb[8];
+            const unsigned char *box = boxes + (wid * kStages + stage) * kTmaBoxBytes + lane * 8;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                wa[i] = *reinterpret_cast<const uint2 *>(box + i * kTmaBoxW);
+                wb[i] = *reinterpret_cast<const uint2 *>(box + (8 + i) * kTmaBoxW);
+            }
+            const bool has_b = by + 1 < job.nbh;
+            uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
+            s576 += fused2_pair<CLS + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
+        }
+        if (!more || c != cur_c) {  // the item closed its chunk: one atomic per warp and chunk
+            const unsigned long long t = warp_sum_u64(s576);
+            if (lane == 0 && t) atomicAdd(a.acc + job.image, t);
+            s576 = 0;
+        }
+        if (!more) break;
+        cur_c = c;
+        citem = item;
+        cch = ch;
+        advance();
+        stage ^= 1;
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// TMA-staged batch launch for exactly r = R (instantiated with the others).
+template <int R>
+cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap, cudaStream_t s) {
+    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
+    return launch_staged(fused2_tma_kernel<R - 1, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+                         (T / 32) * kStages * kTmaBoxBytes, overlap, s, a);
+}
+
 // Launch for exactly r = R retained coefficients: single-plane (a.single) or
 // batch (a.jobs / a.chunks).  Instantiated per R in rdct_fused2_r*.cu.
 // overlap: a programmatic dependent launch on the previous kernel of the

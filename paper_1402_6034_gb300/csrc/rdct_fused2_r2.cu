@@ -11,4 +11,12 @@ template cudaError_t launch_fused2_r<21>(const Fused2Args &, bool, int, bool, cu
 template cudaError_t launch_fused2_r<22>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<23>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<24>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<17>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<18>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<19>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<20>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<21>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<22>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<23>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<24>(const TmaArgs &, int, bool, cudaStream_t);
 }  // namespace rdct

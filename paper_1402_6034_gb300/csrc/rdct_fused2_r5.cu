@@ -11,4 +11,12 @@ template cudaError_t launch_fused2_r<45>(const Fused2Args &, bool, int, bool, cu
 template cudaError_t launch_fused2_r<46>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<47>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<48>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<41>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<42>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<43>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<44>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<45>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<46>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<47>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<48>(const TmaArgs &, int, bool, cudaStream_t);
 }  // namespace rdct

@@ -11,4 +11,12 @@ template cudaError_t launch_fused2_r<53>(const Fused2Args &, bool, int, bool, cu
 template cudaError_t launch_fused2_r<54>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<55>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<56>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<49>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<50>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<51>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<52>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<53>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<54>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<55>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<56>(const TmaArgs &, int, bool, cudaStream_t);
 }  // namespace rdct

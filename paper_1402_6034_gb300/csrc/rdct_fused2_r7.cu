@@ -11,4 +11,12 @@ template cudaError_t launch_fused2_r<61>(const Fused2Args &, bool, int, bool, cu
 template cudaError_t launch_fused2_r<62>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<63>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<64>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<57>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<58>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<59>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<60>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<61>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<62>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<63>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<64>(const TmaArgs &, int, bool, cudaStream_t);
 }  // namespace rdct
