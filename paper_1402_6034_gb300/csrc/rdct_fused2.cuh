@@ -474,38 +474,42 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
     __syncwarp();
 
     // the warp's items, in order: chunks gw, gw + nwarps, ..., each item0 .. item0 + nitems - 1
-    int c = gw, left = 0, item = 0;
+    // (c, left, rp, seg): the next item to request; an item's row pair and
+    // segment are divided out once per chunk and then stepped
+    int c = gw, left = 0, rp = 0, seg = 0, segs = 1;
     Chunk ch{};
     auto load_chunk = [&]() {
         if (c < a.nchunks) {
             ch = a.chunks[c];
-            item = ch.item0;
+            segs = a.jobs[ch.job].segs;
+            rp = ch.item0 / segs;
+            seg = ch.item0 - rp * segs;
             left = ch.nitems;
         }
     };
     auto advance = [&]() {
         if (--left > 0) {
-            ++item;
+            if (++seg == segs) {
+                seg = 0;
+                ++rp;
+            }
         } else {
             c += nwarps;
             load_chunk();
         }
     };
-    auto request = [&](int st) {  // the current (c, item) into stage st
-        if (lane == 0) {
-            const JobDesc &job = a.jobs[ch.job];
-            const int rp = item / job.segs, seg = item - rp * job.segs;
+    auto request = [&](int st) {  // the next item into stage st
+        if (lane == 0)
             tma_request(a.maps + (int64_t)ch.job * kTensorMapBytes, ring + st * kTmaBoxBytes, bar0 + 8 * st,
                         seg * kTmaBoxW, rp * kTmaBoxH);
-        }
     };
 
     load_chunk();
     if (c >= a.nchunks) return;
     request(0);
-    int cur_c = c, citem = item;  // the item in flight in `stage`
+    int cur_c = c, crp = rp, cseg = seg;  // the item in flight in `stage`
     Chunk cch = ch;
-    advance();                     // (c, item): the next item
+    advance();
     uint32_t phase = 0u;           // bit st: parity of stage st's next completion
     unsigned long long s576 = 0;
     int stage = 0;
@@ -524,8 +528,7 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
             break;
         }
         const JobDesc &job = a.jobs[cch.job];
-        const int rp = citem / job.segs, seg = citem - rp * job.segs;
-        const int bx = seg * 32 + lane, by = 2 * rp;
+        const int bx = cseg * 32 + lane, by = 2 * crp;
         if (bx < job.nbw) {
             uint2 wa[8], wb[8];
             const unsigned char *box = boxes + (wid * kStages + stage) * kTmaBoxBytes + lane * 8;
@@ -545,7 +548,8 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
         }
         if (!more) break;
         cur_c = c;
-        citem = item;
+        crp = rp;
+        cseg = seg;
         cch = ch;
         advance();
         stage ^= 1;
