@@ -94,9 +94,9 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     }
     // TMA staging when every plane allows it and its tensor map encodes (two blocks per thread only)
     p->tma = p->tune.blocks_per_thread == 2 && njobs > 0 && tma_available();
-    if (p->tma) p->maps.assign((size_t)njobs * kTensorMapBytes, 0);
+    if (p->tma) p->maps.assign((size_t)njobs * 2 * kTensorMapBytes, 0);
     for (int32_t i = 0; i < njobs && p->tma; ++i)
-        p->tma = tma_encode_plane(p->jobs[i], p->maps.data() + (size_t)i * kTensorMapBytes);
+        p->tma = tma_encode_plane(p->jobs[i], p->maps.data() + (size_t)i * 2 * kTensorMapBytes);
     if (!p->tma) p->maps.clear();
     std::vector<Chunk> ch;
     const int per = p->tune.items_per_chunk;

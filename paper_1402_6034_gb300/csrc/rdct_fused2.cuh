@@ -128,8 +128,10 @@ __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][
 // pair (block a, block b), so each inverse butterfly and each output scaling
 // serves both blocks.  wb is all zeros when the pair has only its upper block
 // (has_b false): a zero block contributes nothing to the error and is not
-// stored.  Returns 576 * SSE of the two blocks.
-template <int R>
+// stored.  Returns 576 * SSE of the two blocks.  SMEM: dst is a shared-memory
+// staging box (row pitch dpitch, 8-byte aligned rows) that a TMA store writes
+// out, rather than the plane itself.
+template <int R, bool SMEM = false>
 __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], uint8_t *dst,
                                                           int64_t dpitch, int dalign, bool has_b) {
     unsigned sumsq = 0;
@@ -202,11 +204,18 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
                 qa[m] = __float_as_int(x);
                 qb[m] = __float_as_int(y);
             }
-            store_row_u8(dst + n * dpitch, dalign, pack4_sat(qa[0], qa[1], qa[2], qa[3]),
-                         pack4_sat(qa[4], qa[5], qa[6], qa[7]));
-            if (has_b)
-                store_row_u8(dst + (8 + n) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
-                             pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+            if constexpr (SMEM) {
+                *reinterpret_cast<uint2 *>(dst + n * dpitch) =
+                    make_uint2(pack4_sat(qa[0], qa[1], qa[2], qa[3]), pack4_sat(qa[4], qa[5], qa[6], qa[7]));
+                *reinterpret_cast<uint2 *>(dst + (8 + n) * dpitch) =
+                    make_uint2(pack4_sat(qb[0], qb[1], qb[2], qb[3]), pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+            } else {
+                store_row_u8(dst + n * dpitch, dalign, pack4_sat(qa[0], qa[1], qa[2], qa[3]),
+                             pack4_sat(qa[4], qa[5], qa[6], qa[7]));
+                if (has_b)
+                    store_row_u8(dst + (8 + n) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
+                                 pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+            }
         }
     }
     return 576ull * (unsigned long long)sumsq - kept;
@@ -425,7 +434,7 @@ constexpr int kTmaBoxW = 256, kTmaBoxH = 16, kTmaBoxBytes = kTmaBoxW * kTmaBoxH;
 struct TmaArgs {
     const JobDesc *jobs;
     const Chunk *chunks;        // items: row pair * segments + segment
-    const unsigned char *maps;  // kTensorMapBytes per job
+    const unsigned char *maps;  // per job: the source plane's tensor map, then the destination's
     int32_t nchunks;
     unsigned long long *acc;    // per-image 576 * SSE
 };
@@ -445,6 +454,19 @@ __device__ __forceinline__ bool tma_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// One lane: write a staged box of the reconstruction to the plane (rows and
+// columns outside the plane are dropped) and close the bulk group.
+__device__ __forceinline__ void tma_store(const unsigned char *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// One lane: wait until the shared memory of every committed store was read.
+__device__ __forceinline__ void tma_store_drain_reads() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 // One lane: expect the box's bytes on the stage's mbarrier and request it.
 __device__ __forceinline__ void tma_request(const unsigned char *map, uint32_t dst, uint32_t mbar, int x, int y) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "n"(kTmaBoxBytes) : "memory");
@@ -455,7 +477,9 @@ __device__ __forceinline__ void tma_request(const unsigned char *map, uint32_t d
         : "memory");
 }
 
-template <int CLS, int THREADS, int MINB>
+// TSTORE: the reconstruction goes out through the box with TMA stores, else
+// with per-thread stores straight from registers.
+template <int CLS, int THREADS, int MINB, bool TSTORE>
 __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs a) {
     constexpr int WARPS = THREADS / 32;
     __shared__ __align__(128) unsigned char boxes[WARPS * kStages * kTmaBoxBytes];
@@ -500,7 +524,7 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
     };
     auto request = [&](int st) {  // the next item into stage st
         if (lane == 0)
-            tma_request(a.maps + (int64_t)ch.job * kTensorMapBytes, ring + st * kTmaBoxBytes, bar0 + 8 * st,
+            tma_request(a.maps + (int64_t)ch.job * 2 * kTensorMapBytes, ring + st * kTmaBoxBytes, bar0 + 8 * st,
                         seg * kTmaBoxW, rp * kTmaBoxH);
     };
 
@@ -515,9 +539,10 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
     int stage = 0;
     while (true) {
         const bool more = c < a.nchunks;
-        if (more) {  // the other stage was read in the previous iteration by every lane
+        if (more) {  // the other stage was read (and stored from) in the previous iteration
             __syncwarp();
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (lane == 0) tma_store_drain_reads();
             request(stage ^ 1);
         }
         const bool got = tma_wait(bar0 + 8 * stage, (phase >> stage) & 1u);
@@ -529,17 +554,30 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
         }
         const JobDesc &job = a.jobs[cch.job];
         const int bx = cseg * 32 + lane, by = 2 * crp;
+        unsigned char *box = boxes + (wid * kStages + stage) * kTmaBoxBytes;
+        const bool store = TSTORE && job.dst != nullptr;
         if (bx < job.nbw) {
             uint2 wa[8], wb[8];
-            const unsigned char *box = boxes + (wid * kStages + stage) * kTmaBoxBytes + lane * 8;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                wa[i] = *reinterpret_cast<const uint2 *>(box + i * kTmaBoxW);
-                wb[i] = *reinterpret_cast<const uint2 *>(box + (8 + i) * kTmaBoxW);
+                wa[i] = *reinterpret_cast<const uint2 *>(box + i * kTmaBoxW + lane * 8);
+                wb[i] = *reinterpret_cast<const uint2 *>(box + (8 + i) * kTmaBoxW + lane * 8);
             }
             const bool has_b = by + 1 < job.nbh;
-            uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
-            s576 += fused2_pair<CLS + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
+            if constexpr (TSTORE) {
+                // the reconstruction replaces the pixels in the box (each lane its own columns)
+                s576 += fused2_pair<CLS + 1, true>(wa, wb, store ? box + lane * 8 : nullptr, kTmaBoxW, 8, has_b);
+            } else {
+                uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
+                s576 += fused2_pair<CLS + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
+            }
+        }
+        if (store) {  // one TMA store of the box; columns and rows outside the plane are dropped
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                tma_store(a.maps + (int64_t)cch.job * 2 * kTensorMapBytes + kTensorMapBytes,
+                          (uint32_t)__cvta_generic_to_shared(box), cseg * kTmaBoxW, crp * kTmaBoxH);
         }
         if (!more || c != cur_c) {  // the item closed its chunk: one atomic per warp and chunk
             const unsigned long long t = warp_sum_u64(s576);
@@ -554,14 +592,22 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
         advance();
         stage ^= 1;
     }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores done before exit
+    __syncwarp();
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+
+// TMA stores of the reconstruction pay where instruction issue binds (they
+// replace sixteen per-thread stores and their address arithmetic per item);
+// at r = 16 the per-thread stores measured as fast.
+constexpr bool tma_store_pays(int R) { return diag_class(R) >= 6; }
 
 // TMA-staged batch launch for exactly r = R (instantiated with the others).
 template <int R>
 cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap, cudaStream_t s) {
     constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
-    return launch_staged(fused2_tma_kernel<R - 1, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+    constexpr bool TS = tma_store_pays(R);
+    return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
                          (T / 32) * kStages * kTmaBoxBytes, overlap, s, a);
 }
 

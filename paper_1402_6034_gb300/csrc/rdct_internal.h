@@ -117,19 +117,21 @@ cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, in
                                  cudaStream_t s);
 cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
                                 int r, int ctas_per_sm, bool overlap, cudaStream_t s);
-// The same kernel with TMA staging, for batch tables whose items are row pair
-// x 32-column segments (tma_items_of) and whose planes have encoded tensor
-// maps (kTensorMapBytes each, see tma_encode_plane).
+// The same kernel with TMA loads and stores, for batch tables whose items are
+// row pair x 32-column segments (tma_items_of) and whose planes have encoded
+// tensor maps (two of kTensorMapBytes each per plane, see tma_encode_plane).
 cudaError_t launch_fused2_tma_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks,
                                     const unsigned char *maps, unsigned long long *acc, int r, int ctas_per_sm,
                                     bool overlap, cudaStream_t s);
 inline int32_t tma_items_of(const JobDesc &j) { return ((j.nbh + 1) / 2) * ((j.nbw + 31) / 32); }
 constexpr int kTensorMapBytes = 128;  // one encoded 2-D tensor map per plane (64-byte aligned in the table)
-// TMA staging needs the plane to start on a 16-byte boundary with a 16-byte
-// multiple pitch, and the driver's tensor-map encoder.
+// TMA staging needs the source plane and the reconstruction (if any) to start
+// on 16-byte boundaries with 16-byte multiple pitches, and the driver's
+// tensor-map encoder.  tma_encode_plane writes the source's map and then the
+// reconstruction's (zeros when there is none) into 2 * kTensorMapBytes.
 bool tma_available();
 bool tma_plane_ok(const JobDesc &j);
-bool tma_encode_plane(const JobDesc &j, unsigned char *map128);
+bool tma_encode_plane(const JobDesc &j, unsigned char *maps256);
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are
