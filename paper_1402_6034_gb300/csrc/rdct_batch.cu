@@ -28,11 +28,14 @@ struct rdct_plan {
     std::vector<JobDesc> jobs;     // host copy, segs computed for the plan's tile
     std::vector<JobDesc> jobs_pp;  // per-plane launches (one block per thread)
     std::vector<Chunk> chunks;
-    int32_t group_begin[kBatchGroups + 1] = {0};  // chunk ranges per launch group
+    // chunk ranges per launch group: groups 0..kBatchGroups-1 per-thread
+    // copies, kBatchGroups.. the same classes with TMA staging
+    int32_t group_begin[2 * kBatchGroups + 1] = {0};
     JobDesc *d_jobs = nullptr;
     Chunk *d_chunks = nullptr;
-    bool tma = false;                // TMA-staged kernel (items: row pair x 32-column segment)
-    std::vector<unsigned char> maps; // one encoded tensor map per job when tma
+    bool tma = false;                // some jobs use the TMA-staged kernel (items: row pair x 32-column segment)
+    std::vector<unsigned char> maps; // two encoded tensor maps per job (zeros for jobs without TMA)
+    std::vector<char> job_tma;       // per job: TMA staging
     unsigned char *d_maps = nullptr;
     // graph cache: one executable per (sse pointer)
     std::mutex mu;
@@ -92,25 +95,38 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
         p->jobs[i] = make_job(j.src, j.dst, j.dst_pitch, nullptr, 0, j.r, j.image, 1);
         p->jobs_pp[i] = p->jobs[i];
     }
-    // TMA staging when every plane allows it and its tensor map encodes (two blocks per thread only)
-    p->tma = p->tune.blocks_per_thread == 2 && njobs > 0 && tma_available();
-    if (p->tma) p->maps.assign((size_t)njobs * 2 * kTensorMapBytes, 0);
-    for (int32_t i = 0; i < njobs && p->tma; ++i)
-        p->tma = tma_encode_plane(p->jobs[i], p->maps.data() + (size_t)i * 2 * kTensorMapBytes);
-    if (!p->tma) p->maps.clear();
+    // TMA staging per job: two blocks per thread, an r where it pays, and a
+    // plane (and reconstruction) whose tensor maps encode
+    const bool tma_ok = p->tune.blocks_per_thread == 2 && njobs > 0 && tma_available();
+    p->job_tma.assign(njobs, 0);
+    p->maps.clear();
+    p->tma = false;
+    if (tma_ok) {
+        p->maps.assign((size_t)njobs * 2 * kTensorMapBytes, 0);
+        for (int32_t i = 0; i < njobs; ++i) {
+            if (!tma_pays(p->jobs[i].r)) continue;
+            p->job_tma[i] = tma_encode_plane(p->jobs[i], p->maps.data() + (size_t)i * 2 * kTensorMapBytes) ? 1 : 0;
+            p->tma = p->tma || p->job_tma[i];
+        }
+        if (!p->tma) p->maps.clear();
+    }
     std::vector<Chunk> ch;
     const int per = p->tune.items_per_chunk;
     for (int32_t i = 0; i < njobs; ++i) {
-        const int items = p->tma && tma_pays(p->jobs[i].r) ? tma_items_of(p->jobs[i]) : strips_of(p->jobs[i], vrows);
-        const int c = fused_class_of(p->jobs[i].r, p->tune.blocks_per_thread);
+        const bool t = p->job_tma[i] != 0;
+        const int items = t ? tma_items_of(p->jobs[i]) : strips_of(p->jobs[i], vrows);
+        const int c = fused_class_of(p->jobs[i].r, p->tune.blocks_per_thread) + (t ? kBatchGroups : 0);
         for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), c});
     }
     std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
     p->chunks = std::move(ch);
     const int bpt = p->tune.blocks_per_thread;
-    for (int g = 0; g <= kBatchGroups; ++g) p->group_begin[g] = 0;
-    for (const Chunk &c : p->chunks) p->group_begin[batch_group_of_class(c.cls, bpt) + 1]++;
-    for (int g = 0; g < kBatchGroups; ++g) p->group_begin[g + 1] += p->group_begin[g];
+    for (int g = 0; g <= 2 * kBatchGroups; ++g) p->group_begin[g] = 0;
+    for (const Chunk &c : p->chunks) {
+        const bool t = c.cls >= kBatchGroups;
+        p->group_begin[batch_group_of_class(c.cls - (t ? kBatchGroups : 0), bpt) + (t ? kBatchGroups : 0) + 1]++;
+    }
+    for (int g = 0; g < 2 * kBatchGroups; ++g) p->group_begin[g + 1] += p->group_begin[g];
 }
 
 // memset -> one persistent kernel per non-empty group, in stream order (the
@@ -120,12 +136,12 @@ cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
     bool first = true;
-    for (int g = 0; g < kBatchGroups && e == cudaSuccess; ++g) {
+    for (int g = 0; g < 2 * kBatchGroups && e == cudaSuccess; ++g) {
         const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
         if (n == 0) continue;
-        if (p->tma && tma_pays(g + 1))
-            e = launch_fused2_tma_batch(p->d_jobs, p->d_chunks + b, n, p->d_maps, acc, g + 1, p->tune.ctas_per_sm,
-                                        !first, s);
+        if (g >= kBatchGroups)
+            e = launch_fused2_tma_batch(p->d_jobs, p->d_chunks + b, n, p->d_maps, acc, g - kBatchGroups + 1,
+                                        p->tune.ctas_per_sm, !first, s);
         else
             e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm,
                                    p->tune.warps_per_cta, p->tune.blocks_per_thread, !first, s);
