@@ -115,3 +115,50 @@ def test_uneven_4096_images(dev):
             assert_u8_close(j.dst.cpu().numpy(), uo, xo, tie_window=1e-6)
             tot += so
         assert sse[int(i)].item() == pytest.approx(tot, rel=1e-9)
+
+
+def test_plane_larger_than_2gib(dev):
+    """One 65536 x 33280 plane (2.18 GB, 35.5 M blocks): byte offsets past 2^31
+    in the single-plane kernel, both batch stagings (r = 16 with TMA, r = 10
+    with per-thread copies), the r sweep and the forward transform (whose
+    int32 output passes 2^31 elements).  Whole-plane SSE against the oracle,
+    three 16-row bands (first rows, the rows that straddle byte 2^31, last
+    rows) element by element."""
+    from paper_1402_6034_gb300 import synth
+    h, w = 33280, 65536
+    pool = synth.field_u8_torch(2048, 2048, 2.0, 7, device=str(dev), planes=4)
+    rng = np.random.Generator(np.random.PCG64(3))
+    img = torch.empty((h, w), dtype=torch.uint8, device=dev)
+    for y in range(0, h, 2048):
+        for x in range(0, w, 2048):
+            k, dy, dx = (int(v) for v in rng.integers(0, [4, 2048, 2048]))
+            tile = torch.roll(pool[k], shifts=(dy, dx), dims=(0, 1))
+            img[y:y + 2048, x:x + 2048] = tile[:min(2048, h - y)]
+    del pool
+    u8, _, sse = rdct.fused(img, 16)
+    d16, d10 = torch.empty_like(img), torch.empty_like(img)
+    plan = rdct.BatchPlan([rdct.BatchJob(img, d16, 16, 0), rdct.BatchJob(img, d10, 10, 1)], 2)
+    sse_b = torch.empty(2, dtype=torch.float64, device=dev)
+    plan.run(sse_b)
+    sw = rdct.sweep([img], rdct.KIND_RDCT)
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(u8, d16), "single-plane and batch (TMA) reconstructions differ"
+    assert sse_b[0].item() == sse.item()
+    assert sw[0, 15].item() == pytest.approx(sse.item(), rel=1e-12)
+    assert sw[0, 9].item() == pytest.approx(sse_b[1].item(), rel=1e-12)
+    del d16
+    host = img.cpu().numpy()
+    _, _, so16, _ = orc.fused(host, 16, want_xhat=False, want_u8=False, nthreads=0)
+    _, _, so10, _ = orc.fused(host, 10, want_xhat=False, want_u8=False, nthreads=0)
+    assert sse.item() == pytest.approx(so16, rel=1e-9)
+    assert sse_b[1].item() == pytest.approx(so10, rel=1e-9)
+    Y = rdct.forward(img)
+    torch.cuda.synchronize()
+    assert Y.numel() > 2 ** 31
+    for y0 in (0, (1 << 31) // w - 8, h - 16):
+        band = np.ascontiguousarray(host[y0:y0 + 16])
+        for r, got in ((16, u8), (10, d10)):
+            xo, uo, _, _ = orc.fused(band, r)
+            assert_u8_close(got[y0:y0 + 16].cpu().numpy(), uo, xo, tie_window=1e-6)
+        assert np.array_equal(Y[y0 // 8:y0 // 8 + 2].cpu().numpy(), orc.forward(band))
