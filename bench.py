@@ -377,13 +377,20 @@ def bench_uneven(args, dev):
             "quality": {"mean_psnr_db": float(psnr.mean())}}
 
 
+def sweep_images(dev, n: int = 1024) -> torch.Tensor:
+    """[n, 512, 512] uint8 1/f^2 images: 64 seeded fields, each also taken at n / 64 - 1 block-aligned
+    circular shifts (distinct block contents per image)."""
+    from paper_1402_6034_gb300 import synth
+    base = torch.from_numpy(synth.image_batch(64, 512, 512, 2.0, 0)).to(dev)
+    return torch.cat([torch.roll(base, shifts=(8 * k, 8 * ((k * 7) % 64)), dims=(1, 2)) for k in range(n // 64)])
+
+
 def bench_sweep(args, dev):
     """1024 images of 512 x 512, r = 1..64 for the RDCT and the exact DCT: one energy pass per transform
     (rdct_sweep), per-r average MSE / PSNR and the MSE absolute percentage error against the DCT."""
-    from paper_1402_6034_gb300 import rdct, synth
+    from paper_1402_6034_gb300 import rdct
     n = 1024
-    base = torch.from_numpy(synth.image_batch(64, 512, 512, 2.0, 0)).to(dev)
-    imgs = torch.cat([torch.roll(base, shifts=(8 * k, 8 * ((k * 7) % 64)), dims=(1, 2)) for k in range(n // 64)])
+    imgs = sweep_images(dev, n)
     planes = rdct.plane_array(imgs)
     out_r = torch.empty((n, 64), dtype=torch.float64, device=dev)
     out_d = torch.empty((n, 64), dtype=torch.float64, device=dev)

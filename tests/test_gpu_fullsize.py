@@ -17,7 +17,7 @@ import torch
 
 from oracle import oracle as orc
 from paper_1402_6034_gb300 import rdct
-from tests.gpu_helpers import assert_u8_close, cuda_or_skip
+from tests.gpu_helpers import assert_sse_close, assert_u8_close, cuda_or_skip
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -162,3 +162,36 @@ def test_plane_larger_than_2gib(dev):
             xo, uo, _, _ = orc.fused(band, r)
             assert_u8_close(got[y0:y0 + 16].cpu().numpy(), uo, xo, tie_window=1e-6)
         assert np.array_equal(Y[y0 // 8:y0 // 8 + 2].cpu().numpy(), orc.forward(band))
+
+
+def test_sweep_1024_images(dev):
+    """The r sweep over 1024 images of 512 x 512 for both transforms, launched
+    as bench.py launches it (one rdct_sweep_noalloc call per transform).
+    Sampled images against the oracle's direct reconstruction at every r;
+    on all images: SSE(r) non-increasing in r, SSE(64) = 0 for the RDCT (the
+    kept set is then the whole block and the transform is orthogonal), and
+    SSE(r) of the RDCT equal to the fused kernel's on a few images."""
+    import bench
+    imgs = bench.sweep_images(dev, 1024)
+    planes = rdct.plane_array(imgs)
+    out_r = torch.empty((1024, 64), dtype=torch.float64, device=dev)
+    out_d = torch.empty((1024, 64), dtype=torch.float64, device=dev)
+    rdct.sweep_noalloc(planes, out_r, rdct.KIND_RDCT)
+    rdct.sweep_noalloc(planes, out_d, rdct.KIND_DCT)
+    torch.cuda.synchronize()
+    r_np, d_np = out_r.cpu().numpy(), out_d.cpu().numpy()
+    for o in (r_np, d_np):
+        assert np.all(np.diff(o, axis=1) <= 1e-6 * np.maximum(o[:, :-1], 1.0))
+    assert np.all(r_np[:, 63] == 0.0)
+    rng = np.random.Generator(np.random.PCG64(4))
+    sample = [0, 63, 64, 1023] + [int(v) for v in rng.integers(0, 1024, 2)]
+    for i in sample:
+        img = imgs[i].cpu().numpy()
+        ref_r = orc.sweep(img, rdct.KIND_RDCT, nthreads=0)
+        ref_d = orc.sweep(img, rdct.KIND_DCT, nthreads=0)
+        np.testing.assert_allclose(r_np[i], ref_r, rtol=1e-9, atol=1e-9)
+        for r in range(1, 65):
+            assert_sse_close(d_np[i, r - 1], ref_d[r - 1], img.size)
+        for r in (4, 16, 45):
+            assert rdct.fused(imgs[i], r, want_u8=False)[2].item() == pytest.approx(r_np[i, r - 1], rel=1e-12,
+                                                                                  abs=1e-12)
