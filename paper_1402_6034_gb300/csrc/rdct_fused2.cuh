@@ -223,15 +223,16 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
 
 // ------------------------------------------------------------------ kernel
 
-// Launch shape per r: 128 registers while r ends on an anti-diagonal up to 7
-// (r <= 36), 168 above, and at most kFused2MaxCtas CTAs of 128 threads per SM
-// (see launch_staged).  Measured: more registers for independent work per
-// thread beat more resident warps, and shared memory beyond four rings
-// squeezes the L1 the copies go through.
+// Launch shape per r: 128 registers (four CTAs of 128 threads per SM) up to
+// r = 26, 168 (three CTAs) above, and never more than kFused2MaxCtas CTAs per
+// SM (see launch_staged).  Measured on a 600-frame 4K clip: four CTAs are 1%
+// faster at r = 25; three are 2% faster at r = 28 and 2-4% at r = 32-36 (no
+// spills), and two CTAs with 255 registers were 4-8% slower from r = 45 up.
+// Shared memory beyond four rings squeezes the L1 the copies go through.
 template <int R>
 struct Fused2Shape {
     static constexpr int threads = 128;
-    static constexpr int min_blocks = diag_class(R) <= 7 ? 4 : 3;
+    static constexpr int min_blocks = R <= 26 ? 4 : 3;
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
