@@ -33,7 +33,7 @@ UNIT = "Gpixel/s"
 # DRAM bytes (read + write) per sample of the fused kernel, from the ncu capture summarised in
 # profiles/fused_video_40x4k_r16_ncu.md.  Reported only while the kernel sources still hash to
 # the value they had when the counters were taken.
-FUSED_TRAFFIC = {"sources_sha256_16": "a72c4021283c2357", "bytes_per_sample": 1.9078}
+FUSED_TRAFFIC = {"sources_sha256_16": "9d20471432b99d22", "bytes_per_sample": 1.9066}
 FUSED_SOURCES = ["rdct_fused2.cuh", "rdct_device.cuh", "rdct_blocks.cuh", "rdct_fused2_launch.cu"]
 
 
@@ -185,8 +185,9 @@ class VideoWorkload:
         self.config = {"workload": self.name, "frames": frames, "planes_per_frame": 3, "r": r,
                        "luma": "3840x2160 1/f^2", "chroma": "2x1920x1080 1/f^3", "samples_per_step": self.samples,
                        "outputs": "uint8 reconstruction of every plane + per-frame SSE",
-                       "l2": "inputs and outputs (2 x 7.46 GB) larger than L2; no flush needed",
-                       "launch": "one CUDA-graph launch per step (persistent kernel over all 1800 planes)"}
+                       "l2": f"inputs and outputs (2 x {self.samples / 1e9:.2f} GB) "
+                             + ("larger than L2; no flush needed" if self.samples > 129e6 else "within L2"),
+                       "launch": f"one CUDA-graph launch per step (persistent kernel over all {3 * frames} planes)"}
         self.kernels_per_step = 2  # fused batch kernel (one r class) + SSE finalize
 
     def step(self, stream):
