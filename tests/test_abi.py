@@ -79,3 +79,17 @@ def test_noalloc_sweep_limits_are_checked_on_the_host():
     planes = (rdct.Plane * 2049)(*([ok] * 2049))
     assert lib.rdct_sweep_noalloc(planes, 2049, 0, ctypes.c_void_p(16), None) == 4
     assert "2048" in _last_error()
+
+
+def test_batch_job_errors_name_the_job_and_keep_the_detail():
+    lib = rdct.load()
+    jobs = (rdct.Job * 2)()
+    jobs[0].src = rdct.Plane(ctypes.c_void_p(16), 16, 16, 8)
+    jobs[0].r, jobs[0].image = 10, 0
+    jobs[1].src = rdct.Plane(ctypes.c_void_p(16), 12, 12, 8)  # width not a multiple of 8
+    jobs[1].r, jobs[1].image = 10, 0
+    h = ctypes.c_void_p()
+    assert lib.rdct_batch_plan_create(jobs, 2, 1, None, ctypes.byref(h)) == 2
+    msg = _last_error()
+    assert "batch job 1" in msg and "multiples of 8" in msg, msg
+    assert not h.value
