@@ -453,10 +453,9 @@ def bench_variants(args, dev):
     """The other transforms of the paper (signed DCT, ceil(2C) polar variant, sign(C) polar, and C_orth
     through the same general kernel) on the 1024 x 512^2 batch at r = 10, timed as one tall plane per call;
     average PSNR and UQI per variant over a 64-image subset at several r."""
-    from paper_1402_6034_gb300 import rdct, synth
+    from paper_1402_6034_gb300 import rdct
     n, r = 1024, 10
-    base = torch.from_numpy(synth.image_batch(64, 512, 512, 2.0, 0)).to(dev)
-    imgs = torch.cat([torch.roll(base, shifts=(8 * k, 8 * ((k * 7) % 64)), dims=(1, 2)) for k in range(n // 64)])
+    imgs = sweep_images(dev, n)
     tall = imgs.view(n * 512, 512)
     out = torch.empty_like(tall)
     sse = torch.empty(1, dtype=torch.float64, device=dev)
@@ -505,7 +504,6 @@ def bench_variants(args, dev):
             "gpu_launches": 2 * args.steps, "per_variant": per, "quality_64_images": quality}
 
 
-# ------------------------------------------------------------------ serving
 # ------------------------------------------------------------------ serving
 
 def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0), seed: int = 0):
