@@ -713,7 +713,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, done, tt = cpu_oracle_rate(wl.cpu_planes(), args.r, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": f"{done} samples (first frames of the same workload), {tt:.1f} s of CPU time"}
+                                "sample": f"{done} samples = {100.0 * done / wl.samples:.0f}% of the same workload "
+                                          f"(its planes in order, up to {args.cpu_seconds:.0f} s), {tt:.1f} s of CPU time"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
