@@ -99,9 +99,12 @@ __device__ __forceinline__ float variant_block(const uint32_t w[16], int r, cons
 }
 
 // Warps take block-row segments of 32 blocks (one block per lane); the plane's
-// squared error is summed per thread in FP64 and added once per warp.
+// squared error is summed per thread in FP64 and added once per warp.  Launch
+// bounds: four CTAs per SM (128 registers) while the class fits without
+// spills (anti-diagonal class up to 3, r <= 10), three up to class 6, two
+// above.
 template <int D>
-__global__ void __launch_bounds__(128, D <= 6 ? 3 : 2) variant_kernel(const JobDesc job, const MatConsts M, double *acc) {
+__global__ void __launch_bounds__(128, D <= 3 ? 4 : D <= 6 ? 3 : 2) variant_kernel(const JobDesc job, const MatConsts M, double *acc) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
