@@ -523,10 +523,15 @@ def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0)
         dst = torch.empty((q.planes, q.side, q.side), dtype=torch.uint8).pin_memory()
         reqs.append((src, dst, q.r, q.t))
     samples = sum(s.numel() for s, _, _, _ in reqs)
-    # warm the library and the device once
-    w = rdct.Server(device_budget_bytes=1 << 28, max_batch=4, streams=1)
-    w.wait(w.submit(reqs[0][0], reqs[0][2], reqs[0][1]))
-    w.close()
+    # warm the library and the device once: one small request for every r, so that the first launch of
+    # each per-r kernel (and its module load) falls outside the timed runs
+    small = torch.from_numpy(synth.image_1f(64, 64, alpha=2.0, seed=seed)).pin_memory()
+    small_out = torch.empty_like(small).pin_memory()
+    for kw in (dict(max_batch=64, streams=2), dict(max_batch=1, streams=1)):
+        w = rdct.Server(device_budget_bytes=1 << 28, **kw)
+        for tk in [w.submit(small, r, small_out) for r in range(1, 65)]:
+            w.wait(tk)
+        w.close()
     rows = []
     for rate in rates:
         row = {"rate_req_s": rate if rate else "saturation"}

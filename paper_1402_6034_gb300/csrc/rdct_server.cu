@@ -114,38 +114,43 @@ rdct_status validate_request(const rdct_request *q) {
     return RDCT_OK;
 }
 
-bool grow(Lane &L, int32_t njobs, int32_t nchunks, int32_t nacc) {
-    if (njobs > L.cap_jobs) {
-        cudaFree(L.d_jobs);
-        cudaFreeHost(L.h_jobs);
-        L.d_jobs = nullptr;
-        L.h_jobs = nullptr;
-        L.cap_jobs = std::max(njobs, 2 * L.cap_jobs);
-        if (cudaMalloc(&L.d_jobs, L.cap_jobs * sizeof(JobDesc)) != cudaSuccess ||
-            cudaMallocHost(&L.h_jobs, L.cap_jobs * sizeof(JobDesc)) != cudaSuccess)
-            return false;
-    }
-    if (nchunks > L.cap_chunks) {
-        cudaFree(L.d_chunks);
-        cudaFreeHost(L.h_chunks);
-        L.d_chunks = nullptr;
-        L.h_chunks = nullptr;
-        L.cap_chunks = std::max(nchunks, 2 * L.cap_chunks);
-        if (cudaMalloc(&L.d_chunks, L.cap_chunks * sizeof(Chunk)) != cudaSuccess ||
-            cudaMallocHost(&L.h_chunks, L.cap_chunks * sizeof(Chunk)) != cudaSuccess)
-            return false;
-    }
-    if (nacc > L.cap_acc) {
-        cudaFree(L.d_acc);
-        cudaFreeHost(L.h_acc);
-        L.d_acc = nullptr;
-        L.h_acc = nullptr;
-        L.cap_acc = std::max(nacc, 2 * L.cap_acc);
-        if (cudaMalloc(&L.d_acc, L.cap_acc * sizeof(unsigned long long)) != cudaSuccess ||
-            cudaMallocHost(&L.h_acc, L.cap_acc * sizeof(unsigned long long)) != cudaSuccess)
-            return false;
+// Grows one table pair (device + pinned host) of a lane to at least n
+// elements.  Called only while the lane is idle (its last batch completed),
+// so the old device table is released in stream order instead of by a
+// device-wide synchronising cudaFree.  Tables are sized at server creation
+// for a full budget, so this runs only for unusually fragmented batches.
+template <typename T>
+bool grow_table(cudaStream_t s, T *&d, T *&h, int32_t &cap, int32_t n) {
+    if (n <= cap) return true;
+    if (d) cudaFreeAsync(d, s);
+    if (h) cudaFreeHost(h);
+    d = nullptr;
+    h = nullptr;
+    cap = std::max(n, 2 * cap);
+    if (cudaMallocAsync(reinterpret_cast<void **>(&d), (size_t)cap * sizeof(T), s) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void **>(&h), (size_t)cap * sizeof(T)) != cudaSuccess) {
+        cap = 0;
+        return false;
     }
     return true;
+}
+
+bool grow(Lane &L, int32_t njobs, int32_t nchunks, int32_t nacc) {
+    return grow_table(L.s, L.d_jobs, L.h_jobs, L.cap_jobs, njobs) &&
+           grow_table(L.s, L.d_chunks, L.h_chunks, L.cap_chunks, nchunks) &&
+           grow_table(L.s, L.d_acc, L.h_acc, L.cap_acc, nacc);
+}
+
+// Chunks a batch can need when the whole budget holds its planes: a chunk
+// covers kServerItemsPerChunk items of 32 column pairs, and a pair holds at
+// least one 8x8 block of input (two unless it is in the last block row of a
+// plane with an odd number of them); every plane adds at most one partial
+// chunk.  Capped so that a very large budget does not pin a large table up
+// front (larger batches still grow the table).
+int32_t chunk_bound(const rdct_server_opts &o) {
+    const int64_t chunk_input = (int64_t)kServerItemsPerChunk * 32 * 64;
+    const int64_t n = o.device_budget_bytes / 2 / chunk_input + 8 * (int64_t)o.max_batch + 64;
+    return (int32_t)std::min<int64_t>(n, 1 << 20);
 }
 
 void finish(rdct_server *S, Req &r, rdct_status st, Clock::time_point now) {
@@ -279,7 +284,11 @@ void scheduler(rdct_server *S) {
                 L.batch.push_back(S->ready.front());
                 S->ready.pop_front();
             }
+            // the batch's requests are admitted (not cancellable) and only this
+            // thread touches the lane, so submitters need not wait for the launch
+            lk.unlock();
             const rdct_status st = launch_batch(S, L);
+            lk.lock();
             S->batches++;
             if (st != RDCT_OK) {
                 const Clock::time_point t = Clock::now();
@@ -318,11 +327,11 @@ double percentile(std::vector<double> v, double p) {
 void server_free(rdct_server *S) {
     for (Lane &L : S->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
-        cudaFree(L.d_jobs);
+        if (L.d_jobs) cudaFree(L.d_jobs);
         cudaFreeHost(L.h_jobs);
-        cudaFree(L.d_chunks);
+        if (L.d_chunks) cudaFree(L.d_chunks);
         cudaFreeHost(L.h_chunks);
-        cudaFree(L.d_acc);
+        if (L.d_acc) cudaFree(L.d_acc);
         cudaFreeHost(L.h_acc);
         if (L.done) cudaEventDestroy(L.done);
         if (L.s) cudaStreamDestroy(L.s);
@@ -365,7 +374,8 @@ rdct_status rdct_server_create(const rdct_server_opts *opts, rdct_server **serve
     for (Lane &L : S->lanes) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-        if (e == cudaSuccess && !grow(L, 64, 1024, opts->max_batch)) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess && !grow(L, 4 * opts->max_batch, chunk_bound(*opts), opts->max_batch))
+            e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
         server_free(S);
