@@ -245,15 +245,22 @@ typedef struct {
 
 typedef struct rdct_plan rdct_plan;
 
-/* Build a plan over `njobs` planes: a flattened index of 8-row strips over
- * all planes, grouped into chunks (one descriptor per chunk), uploaded to
- * the device once.  tune may be NULL (defaults / autotune cache).  All job
- * pointers must stay valid while the plan is used. */
+/* Build a plan over `njobs` planes: every plane is cut into work items
+ * (runs of 32 column pairs, a pair being two vertically adjacent 8x8 blocks;
+ * for planes that take TMA staging, 32-column segments of a row pair),
+ * items are grouped into chunks ordered by r, and the job and chunk tables
+ * (and the planes' tensor maps) are uploaded to the device once.  tune may be
+ * NULL (defaults / autotune cache).  All job pointers must stay valid while
+ * the plan is used.  Errors: RDCT_ERR_ARG / RDCT_ERR_SHAPE naming the first
+ * bad job, RDCT_ERR_OOM, RDCT_ERR_CUDA. */
 RDCT_API rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t nimages, const rdct_tune *tune,
                                    rdct_plan **plan);
-/* Run the whole batch as ONE persistent launch; the launch sequence is
- * captured into a CUDA graph on the first run on a given stream and replayed
- * afterwards.  sse_per_image: DEVICE, [nimages] doubles, overwritten. */
+/* Run the whole batch as one CUDA-graph launch: reset of the error slots,
+ * one persistent kernel per r present (two where planes of that r take
+ * different stagings), conversion of the slots to SSE.  The sequence is
+ * captured on the first run with a given sse_per_image pointer and replayed
+ * afterwards on `stream`.  sse_per_image: DEVICE, [nimages] doubles, 8-byte
+ * aligned, overwritten. */
 RDCT_API rdct_status rdct_batch_run(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
 /* Same work with one plain launch per plane (the baseline batching is
  * compared against). */
