@@ -2,11 +2,13 @@
 // autotuner that picks the launch shape.
 //
 // The paper runs its experiment image by image (Sec. 3).  Here every plane of
-// a batch is cut into strips (one block row, 32 blocks wide), strips are
-// grouped into chunks, and the chunk table is walked by persistent warps, so a
-// batch of thousands of planes of different sizes and r costs one graph
-// launch.  The retained-coefficient count r varies per plane; chunks are
-// ordered by r and each r present gets its own specialised kernel launch.
+// a batch is cut into work items (32 column pairs of two 8x8 blocks for the
+// per-thread-copy kernel, a 32-column segment of a row pair for the TMA-staged
+// one; one block row of 32 blocks for the scalar kernel), items are grouped
+// into chunks, and the chunk table is walked by persistent warps, so a batch
+// of thousands of planes of different sizes and r costs one graph launch.
+// The retained-coefficient count r varies per plane; chunks are ordered by r
+// (and staging form) and each group gets its own specialised kernel launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
