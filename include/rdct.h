@@ -99,7 +99,11 @@ RDCT_API const char *rdct_status_string(rdct_status s);
 RDCT_API size_t rdct_last_error(char *buf, size_t cap);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 RDCT_API int32_t rdct_version(void);
-/* Blocks the host until all work on `stream` is done; reports async errors. */
+/* Blocks the host until all work on `stream` is done; reports async errors
+ * (RDCT_ERR_CUDA).  Returns RDCT_ERR_TIMEOUT when a TMA-staged batch kernel
+ * gave up waiting for a staged tile since the last check (its warp stopped
+ * early, so that launch's outputs and errors are incomplete); the count is
+ * reset by the check. */
 RDCT_API rdct_status rdct_sync(rdct_stream stream);
 
 /* ------------------------------------------------------- the method's steps */

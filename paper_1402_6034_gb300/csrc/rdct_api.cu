@@ -151,6 +151,13 @@ int32_t rdct_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 rdct_status rdct_sync(rdct_stream stream) {
     RDCT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     RDCT_CUDA_TRY(cudaGetLastError());
+    const unsigned int t = take_tma_timeouts_r0() + take_tma_timeouts_r1() + take_tma_timeouts_r2() +
+                           take_tma_timeouts_r3() + take_tma_timeouts_r4() + take_tma_timeouts_r5() +
+                           take_tma_timeouts_r6() + take_tma_timeouts_r7();
+    if (t)
+        return set_error(RDCT_ERR_TIMEOUT, "rdct_sync: " + std::to_string(t) +
+                                               " TMA waits for a staged box ran out; the launches that hit them "
+                                               "stopped early and their results are incomplete");
     return RDCT_OK;
 }
 

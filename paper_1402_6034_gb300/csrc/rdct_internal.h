@@ -132,6 +132,17 @@ constexpr int kTensorMapBytes = 128;  // one encoded 2-D tensor map per plane (6
 bool tma_available();
 bool tma_plane_ok(const JobDesc &j);
 bool tma_encode_plane(const JobDesc &j, unsigned char *maps256);
+// TMA-staged kernels bound their waits for a staged box; a warp whose wait
+// runs out counts it and stops.  Each translation unit that instantiates
+// those kernels holds its own counter; these read and clear them.
+unsigned int take_tma_timeouts_r0();
+unsigned int take_tma_timeouts_r1();
+unsigned int take_tma_timeouts_r2();
+unsigned int take_tma_timeouts_r3();
+unsigned int take_tma_timeouts_r4();
+unsigned int take_tma_timeouts_r5();
+unsigned int take_tma_timeouts_r6();
+unsigned int take_tma_timeouts_r7();
 // In-place conversion of n uint64 576*SSE slots to double SSE.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are

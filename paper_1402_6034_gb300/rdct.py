@@ -165,6 +165,11 @@ def exported_names() -> list[str]:
     return [n for n in _SIGS if getattr(lib, n, None) is not None]
 
 
+def sync(stream=None) -> None:
+    """rdct_sync: wait for the work on `stream` and raise on an asynchronous error (RdctError)."""
+    _check(load().rdct_sync(_stream(stream)), "rdct_sync")
+
+
 def _check(status: int, what: str):
     if status != 0:
         lib = load()

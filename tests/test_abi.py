@@ -93,3 +93,8 @@ def test_batch_job_errors_name_the_job_and_keep_the_detail():
     msg = _last_error()
     assert "batch job 1" in msg and "multiples of 8" in msg, msg
     assert not h.value
+
+
+def test_binding_has_sync():
+    assert callable(rdct.sync)
+    assert "rdct_sync" in rdct._SIGS

@@ -60,7 +60,7 @@ def test_batch_graph_matches_oracle(dev, pitch_pad):
     sse = torch.empty(len(specs), dtype=torch.float64, device=dev)
     plan.run(sse)
     plan.run(sse)  # graph replay
-    torch.cuda.synchronize()
+    rdct.sync()  # raises on an asynchronous error or a TMA wait that ran out
     _check_against_oracle(specs, jobs, host, sse.cpu().numpy())
     plan.close()
 
@@ -112,7 +112,7 @@ def test_batch_mixed_staging(dev):
     plan = rdct.BatchPlan(jobs, len(shapes))
     sse = torch.empty(len(shapes), dtype=torch.float64, device=dev)
     plan.run(sse)
-    torch.cuda.synchronize()
+    rdct.sync()
     _check_against_oracle(specs, jobs, host, sse.cpu().numpy())
     outs = [j.dst.clone() if j.dst is not None else None for j in jobs]
     sse_p = torch.empty(len(shapes), dtype=torch.float64, device=dev)

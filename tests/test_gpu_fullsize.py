@@ -49,7 +49,7 @@ def test_video_600_frames_4k_r16(dev):
     stream = torch.cuda.current_stream()
     wl.step(stream)
     wl.step(stream)  # graph replay, as in the timed loop
-    torch.cuda.synchronize()
+    rdct.sync(stream)
     sse = wl.sse.clone()
     # independent kernel: the sweep's SSE(16) summed over the three planes of each frame
     sw = torch.zeros(600, dtype=torch.float64, device=dev)
