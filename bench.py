@@ -164,6 +164,23 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workloads
 
+def video_config(frames: int, r: int) -> dict:
+    """The `config` of the video workload (shared by both bench arms)."""
+    samples = frames * (3840 * 2160 + 2 * 1920 * 1080)
+    return {"workload": f"video_yuv420_{frames}x3840x2160_r{r}", "frames": frames, "planes_per_frame": 3, "r": r,
+            "luma": "3840x2160 1/f^2", "chroma": "2x1920x1080 1/f^3", "samples_per_step": samples,
+            "outputs": "uint8 reconstruction of every plane + per-frame SSE",
+            "l2": f"inputs and outputs (2 x {samples / 1e9:.2f} GB) "
+                  + ("larger than L2; no flush needed" if samples > 129e6 else "within L2"),
+            "launch": f"one CUDA-graph launch per step (persistent kernel over all {3 * frames} planes)"}
+
+
+def batch512_config(r: int) -> dict:
+    """The `config` of the 1024 x 512 x 512 batch workload (shared by both bench arms)."""
+    return {"workload": f"batch_1024x512x512_r{r}", "images": 1024, "r": r, "samples_per_step": 1024 * 512 * 512,
+            "l2": "inputs and outputs (2 x 268 MB) larger than L2; no flush needed"}
+
+
 class VideoWorkload:
     def __init__(self, frames: int, r: int, dev):
         from paper_1402_6034_gb300 import rdct, synth
@@ -181,13 +198,9 @@ class VideoWorkload:
         self.nimages = frames
         self.plan = rdct.BatchPlan(jobs, frames)
         self.sse = torch.empty(frames, dtype=torch.float64, device=dev)
-        self.name = f"video_yuv420_{frames}x3840x2160_r{r}"
-        self.config = {"workload": self.name, "frames": frames, "planes_per_frame": 3, "r": r,
-                       "luma": "3840x2160 1/f^2", "chroma": "2x1920x1080 1/f^3", "samples_per_step": self.samples,
-                       "outputs": "uint8 reconstruction of every plane + per-frame SSE",
-                       "l2": f"inputs and outputs (2 x {self.samples / 1e9:.2f} GB) "
-                             + ("larger than L2; no flush needed" if self.samples > 129e6 else "within L2"),
-                       "launch": f"one CUDA-graph launch per step (persistent kernel over all {3 * frames} planes)"}
+        self.config = video_config(frames, r)
+        self.name = self.config["workload"]
+        assert self.config["samples_per_step"] == self.samples
         self.kernels_per_step = 2  # fused batch kernel (one r class) + SSE finalize
 
     def step(self, stream):
@@ -236,9 +249,8 @@ class Batch512Workload(VideoWorkload):
         self.nimages = n
         self.plan = rdct.BatchPlan(self.jobs, n)
         self.sse = torch.empty(n, dtype=torch.float64, device=dev)
-        self.name = f"batch_1024x512x512_r{r}"
-        self.config = {"workload": self.name, "images": n, "r": r, "samples_per_step": self.samples,
-                       "l2": "inputs and outputs (2 x 268 MB) larger than L2; no flush needed"}
+        self.config = batch512_config(r)
+        self.name = self.config["workload"]
         self.kernels_per_step = 2
 
     def host_jobs(self):
@@ -579,13 +591,17 @@ def run_reference(args, rank, world):
     if args.workload == "video":
         Y, U, V = synth.video_yuv420(frames_needed, 2160, 3840, seed=0, device="cpu")
         samples = [[Y[f].numpy(), U[f].numpy(), V[f].numpy()] for f in range(frames_needed)]
-        name = f"video_yuv420_{args.frames}x3840x2160_r{args.r}"
+        config = video_config(args.frames, args.r)
         sample_desc = "one 3840x2160 YUV 4:2:0 frame (3 planes) per step, cycling over the first frames"
-    else:
+    elif args.workload == "batch512":
         imgs = synth.image_batch(frames_needed, 512, 512, 2.0, 0)
         samples = [[imgs[f]] for f in range(frames_needed)]
-        name = f"batch_1024x512x512_r{args.r}"
+        config = batch512_config(args.r)
         sample_desc = "one 512x512 image per step"
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle arm times the video and batch512 "
+                                                             f"workloads, not {args.workload}"}), flush=True)
+        return
     threads = orc.max_threads()
 
     def one(k):
@@ -606,7 +622,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "r": args.r},
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
