@@ -45,6 +45,9 @@ def test_workload_configs():
     assert "larger than L2" in c["l2"] and "1800 planes" in c["launch"]
     small = bench.video_config(1, 16)
     assert small["samples_per_step"] == 12_441_600
+    from paper_1402_6034_gb300 import synth
+    planes = synth.video_yuv420(1, 2160, 3840, seed=0, device="cpu")  # what the GPU arm allocates per frame
+    assert sum(p.numel() for p in planes) == small["samples_per_step"]
     b = bench.batch512_config(10)
     assert b["samples_per_step"] == 1024 * 512 * 512 and b["workload"] == "batch_1024x512x512_r10"
 
