@@ -241,8 +241,10 @@ typedef struct {
 /* Launch shape of the persistent fused kernel. */
 typedef struct {
     int32_t warps_per_cta;   /* 1..8 */
-    int32_t ctas_per_sm;     /* grid = ctas_per_sm * SM count */
-    int32_t items_per_chunk; /* strips handed to a warp at a time */
+    int32_t ctas_per_sm;     /* grid = ctas_per_sm * SM count; 0 = as many as fit (at most 4 for
+                                blocks_per_thread 2) */
+    int32_t items_per_chunk; /* work items handed to a warp at a time (an item is one row of 32
+                                lanes' blocks or block pairs) */
     int32_t blocks_per_thread; /* 2: dp4a/f32x2 kernel, two vertically adjacent 8x8 blocks per
                                   thread, 4 warps per CTA; 1: scalar kernel, one block per thread */
 } rdct_tune;
