@@ -272,6 +272,10 @@ RDCT_API rdct_status rdct_batch_run(rdct_plan *plan, double *sse_per_image, rdct
  * compared against). */
 RDCT_API rdct_status rdct_batch_run_per_plane(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
 RDCT_API rdct_status rdct_batch_plan_get_tune(const rdct_plan *plan, rdct_tune *tune);
+/* Kernels one rdct_batch_run launches (host): one per non-empty group of
+ * chunks (an r, or a register class for the scalar kernel, and a staging
+ * form) plus the conversion of the error slots.  RDCT_ERR_ARG on NULL. */
+RDCT_API rdct_status rdct_batch_plan_kernels(const rdct_plan *plan, int32_t *kernels_per_run);
 RDCT_API rdct_status rdct_batch_plan_destroy(rdct_plan *plan);
 
 /* Time candidate launch shapes on this batch (CUDA events, repeated runs)

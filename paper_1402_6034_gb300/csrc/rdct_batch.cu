@@ -277,6 +277,14 @@ rdct_status rdct_batch_run_per_plane(rdct_plan *p, double *sse, rdct_stream stre
     return RDCT_OK;
 }
 
+rdct_status rdct_batch_plan_kernels(const rdct_plan *p, int32_t *kernels_per_run) {
+    if (!p || !kernels_per_run) return set_error(RDCT_ERR_ARG, "rdct_batch_plan_kernels: null argument");
+    int32_t k = 1;  // the in-place 576*SSE -> SSE conversion
+    for (int g = 0; g < 2 * kBatchGroups; ++g) k += p->group_begin[g + 1] > p->group_begin[g] ? 1 : 0;
+    *kernels_per_run = k;
+    return RDCT_OK;
+}
+
 rdct_status rdct_batch_plan_get_tune(const rdct_plan *p, rdct_tune *tune) {
     if (!p || !tune) return set_error(RDCT_ERR_ARG, "rdct_batch_plan_get_tune: null argument");
     *tune = p->tune;

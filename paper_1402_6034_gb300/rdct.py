@@ -110,6 +110,7 @@ _SIGS = {
     "rdct_batch_run": [_vp, _vp, _vp],
     "rdct_batch_run_per_plane": [_vp, _vp, _vp],
     "rdct_batch_plan_get_tune": [_vp, ctypes.POINTER(Tune)],
+    "rdct_batch_plan_kernels": [_vp, ctypes.POINTER(_i32)],
     "rdct_batch_plan_destroy": [_vp],
     "rdct_autotune": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), _vp],
     "rdct_pipeline_create": [_i64, _i32, ctypes.POINTER(_vp)],
@@ -401,6 +402,12 @@ class BatchPlan:
         t = Tune()
         _check(load().rdct_batch_plan_get_tune(self._h, ctypes.byref(t)), "rdct_batch_plan_get_tune")
         return t.as_dict()
+
+    def kernels_per_run(self) -> int:
+        """Kernels one run launches (one per non-empty chunk group, plus the error conversion)."""
+        k = _i32()
+        _check(load().rdct_batch_plan_kernels(self._h, ctypes.byref(k)), "rdct_batch_plan_kernels")
+        return int(k.value)
 
     def run(self, sse: torch.Tensor, stream=None):
         _check(load().rdct_batch_run(self._h, sse.data_ptr(), _stream(stream)), "rdct_batch_run")

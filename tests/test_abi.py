@@ -98,3 +98,10 @@ def test_batch_job_errors_name_the_job_and_keep_the_detail():
 def test_binding_has_sync():
     assert callable(rdct.sync)
     assert "rdct_sync" in rdct._SIGS
+
+
+def test_batch_plan_kernels_rejects_null():
+    lib = rdct.load()
+    k = ctypes.c_int32(-1)
+    assert lib.rdct_batch_plan_kernels(None, ctypes.byref(k)) == 1
+    assert k.value == -1

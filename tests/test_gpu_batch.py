@@ -109,7 +109,11 @@ def test_batch_mixed_staging(dev):
         jobs.append(rdct.BatchJob(src, dst, r, i))
         host.append((img, r, i))
     specs = list(range(len(shapes)))
-    plan = rdct.BatchPlan(jobs, len(shapes))
+    # the two-block kernel (the one with both stagings), whatever the autotune cache holds
+    plan = rdct.BatchPlan(jobs, len(shapes), tune={"warps_per_cta": 4, "ctas_per_sm": 0, "items_per_chunk": 16,
+                                                   "blocks_per_thread": 2})
+    nr = len({r for *_, r in shapes})
+    assert nr + 1 <= plan.kernels_per_run() <= 2 * nr + 1  # per r: one or two stagings; + error conversion
     sse = torch.empty(len(shapes), dtype=torch.float64, device=dev)
     plan.run(sse)
     rdct.sync()
