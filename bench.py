@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the r table, the uneven batch, the r sweep and the separate steps")
     return ap.parse_args()
 
 
@@ -265,10 +267,34 @@ class Batch512Workload(VideoWorkload):
 
 
 
-def cpu_oracle_rate(planes_iter, r: int, budget_s: float):
-    """Times the FP64 oracle (all host threads) over planes until budget_s has passed."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and its architecture."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()}, {os.cpu_count()} logical CPUs)"
+
+
+def cpu_oracle_rate(planes_iter, r: int, budget_s: float, threads: int = 0):
+    """Times the FP64 oracle over planes until budget_s has passed (threads 0: all host threads)."""
     from oracle import oracle as orc
-    threads = orc.max_threads()
+    threads = threads or orc.max_threads()
     done, t_total = 0, 0.0
     for img in planes_iter:
         t = time.perf_counter()
@@ -400,7 +426,9 @@ def sweep_images(dev, n: int = 1024) -> torch.Tensor:
 
 def bench_sweep(args, dev):
     """1024 images of 512 x 512, r = 1..64 for the RDCT and the exact DCT: one energy pass per transform
-    (rdct_sweep), per-r average MSE / PSNR and the MSE absolute percentage error against the DCT."""
+    (rdct_sweep_noalloc, the allocation-free form of rdct_sweep: the same kernels, with its descriptor tables
+    in the library's fixed array), per-r average MSE / PSNR and the MSE absolute percentage error against
+    the DCT."""
     from paper_1402_6034_gb300 import rdct
     n = 1024
     imgs = sweep_images(dev, n)
@@ -518,23 +546,27 @@ def bench_variants(args, dev):
 
 # ------------------------------------------------------------------ serving
 
-def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0), seed: int = 0):
+def serving_bench(dev, n_requests: int = 2000, rates=(250.0, 500.0, 1000.0, 2000.0, 4000.0, 0.0), seed: int = 0,
+                  budget: int = 1 << 30):
     """Poisson arrivals of images (side log-uniform 256..4096, 1 or 3 planes, r ~ U{1..64}) against
-    the continuous-batching server and against one launch per image (max_batch 1, one stream).
-    Rate 0 submits everything at once (saturation).  Host buffers are pinned."""
+    the continuous-batching server and against one launch per image (max_batch 1, one stream), both
+    with the same device budget (small enough that admission binds when requests pile up).
+    Rate 0 submits everything at once (saturation).  Requests are windows of one pinned 3 x 4096 x 4096
+    field (rows 4096 bytes apart), and their reconstructions go to the same windows of one pinned output
+    field, so thousands of requests need no per-request host buffers."""
     from paper_1402_6034_gb300 import rdct, synth
-    pool = synth.field_u8_torch(4096, 4096, 2.0, seed, device=str(dev), planes=3).cpu()
+    pool = synth.field_u8_torch(4096, 4096, 2.0, seed, device=str(dev), planes=3).cpu().pin_memory()
+    out_pool = torch.empty_like(pool).pin_memory()
     trace = synth.poisson_trace(1.0, n_requests, seed=seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     reqs = []
     for q in trace:
         y0 = 8 * int(rng.integers(0, (4096 - q.side) // 8 + 1))
         x0 = 8 * int(rng.integers(0, (4096 - q.side) // 8 + 1))
-        src = torch.empty((q.planes, q.side, q.side), dtype=torch.uint8).pin_memory()
-        src.copy_(pool[:q.planes, y0:y0 + q.side, x0:x0 + q.side])
-        dst = torch.empty((q.planes, q.side, q.side), dtype=torch.uint8).pin_memory()
+        src = pool[:q.planes, y0:y0 + q.side, x0:x0 + q.side]
+        dst = out_pool[:q.planes, y0:y0 + q.side, x0:x0 + q.side]
         reqs.append((src, dst, q.r, q.t))
-    samples = sum(s.numel() for s, _, _, _ in reqs)
+    samples = sum(src.numel() for src, _, _, _ in reqs)
     # warm the library and the device once: one small request for every r, so that the first launch of
     # each per-r kernel (and its module load) falls outside the timed runs
     small = torch.from_numpy(synth.image_1f(64, 64, alpha=2.0, seed=seed)).pin_memory()
@@ -547,9 +579,9 @@ def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0)
     rows = []
     for rate in rates:
         row = {"rate_req_s": rate if rate else "saturation"}
-        sses = {}
+        errs = {}
         for name, kw in (("served", dict(max_batch=64, streams=2)), ("plain", dict(max_batch=1, streams=1))):
-            srv = rdct.Server(device_budget_bytes=8 << 30, queue_capacity=n_requests + 1, **kw)
+            srv = rdct.Server(device_budget_bytes=budget, queue_capacity=n_requests + 1, **kw)
             t0 = time.perf_counter()
             tickets = []
             for src, dst, r, t in reqs:
@@ -565,18 +597,77 @@ def serving_bench(dev, n_requests: int = 120, rates=(200.0, 1000.0, 4000.0, 0.0)
             res = [srv.wait(tk) for tk in tickets]
             st = srv.stats()
             srv.close()
-            sses[name] = [x["sse"] for x in res]
+            errs[name] = [(x["sse"], x["sse_u8"]) for x in res]
             psnrs = [x["psnr"] for x in res if math.isfinite(x["psnr"])]
+            psnrs8 = [x["psnr_u8"] for x in res if math.isfinite(x["psnr_u8"])]
             row[name] = {"p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
-                         "mean_ms": st["mean_us"] / 1e3, "gpixels_per_s": st["gpixels_per_s"],
-                         "launches": st["batches"], "mean_psnr_db": float(np.mean(psnrs)) if psnrs else None}
-        row["sse_identical"] = sses["served"] == sses["plain"]
+                         "p999_ms": st["p999_us"] / 1e3, "mean_ms": st["mean_us"] / 1e3,
+                         "gpixels_per_s": st["gpixels_per_s"], "launches": st["batches"],
+                         "peak_resident_bytes": st["peak_resident_bytes"], "rejected": st["rejected"],
+                         "mean_psnr_db": float(np.mean(psnrs)) if psnrs else None,
+                         "mean_psnr_u8_db": float(np.mean(psnrs8)) if psnrs8 else None}
+        row["sse_identical"] = errs["served"] == errs["plain"]
         rows.append(row)
     return {"requests": n_requests, "samples": samples, "sides": "log-uniform 256..4096, square",
-            "planes": "1 or 3", "r": "uniform 1..64", "host_buffers": "pinned",
-            "served": "max_batch 64, 2 compute streams, 8 GiB device budget",
-            "plain": "one launch per image (max_batch 1, 1 stream), same admission and copies",
+            "planes": "1 or 3", "r": "uniform 1..64", "host_buffers": "pinned, windows of one field",
+            "budget_bytes": budget,
+            "served": f"max_batch 64, 2 compute streams, {budget >> 20} MiB device budget",
+            "plain": "one launch per image (max_batch 1, 1 stream), same budget, admission and copies",
             "latency": "submit to completion (C++ steady clock)", "rates": rows}
+
+
+def fused_r_table(wl, rs, steps, warmup, dev):
+    """The default workload's fused path at other r: one graph launch per step over all planes."""
+    from paper_1402_6034_gb300 import rdct
+    peak, kind = peaks()
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for r in rs:
+        jobs = [rdct.BatchJob(j.src, j.dst, r, j.image) for j in wl.jobs]
+        plan = rdct.BatchPlan(jobs, wl.nimages)
+        sse = torch.empty(wl.nimages, dtype=torch.float64, device=dev)
+        ms = events_time(lambda: plan.run(sse, stream), steps, warmup, stream)
+        alg = 2 * wl.samples + 8 * wl.nimages
+        mse = sse.cpu().numpy() / (wl.samples / wl.nimages)
+        rows[str(r)] = {"gpixel_s": wl.samples / (ms / 1e3) / 1e9, "ms": ms,
+                        "frac": alg / (ms / 1e3) / 1e9 / peak, "kernels_per_step": plan.kernels_per_run(),
+                        "form": "dropped coefficients" if r > 32 else "kept coefficients",
+                        "mean_psnr_db": float(np.mean(10 * np.log10(255.0 ** 2 / np.maximum(mse, 1e-300))))}
+        plan.close()
+    return {"workload": wl.name.replace(f"_r{wl.r}", "_r*"), "peak_source": f"{kind} hbm_gbs", "steps": steps,
+            "per_r": rows}
+
+
+def bench_steps(dev, steps: int, warmup: int, r: int = 10):
+    """The separate calls of the method (rdct_forward, rdct_compress, rdct_inverse, rdct_mse_psnr) on the
+    1024 x 512^2 batch taken as one 512 x 524288 plane, each against its algorithmic bytes."""
+    from paper_1402_6034_gb300 import rdct
+    peak, kind = peaks()
+    imgs = sweep_images(dev, 1024)
+    tall = imgs.view(1024 * 512, 512)
+    npx = tall.numel()
+    nblk = npx // 64
+    stream = torch.cuda.current_stream()
+    Y = rdct.forward(tall, stream)
+    Yc = rdct.compress(Y, r, stream)
+    rec = rdct.inverse(Yc, 512 // 8, 1024 * 512 // 8, r, stream=stream)[0]
+    calls = {
+        "rdct_forward": (lambda: rdct.forward(tall, stream), 5 * npx, "1 B read + 4 B int32 write per pixel"),
+        "rdct_compress": (lambda: rdct.compress(Y, r, stream), (256 + 4 * r) * nblk,
+                          f"256 B read + {4 * r} B write per block (r = {r})"),
+        "rdct_inverse": (lambda: rdct.inverse(Yc, 512 // 8, 1024 * 512 // 8, r, stream=stream), (4 * r + 64) * nblk,
+                         f"{4 * r} B read + 64 B uint8 write per block"),
+        "rdct_mse_psnr": (lambda: rdct.mse_psnr(tall, rec, stream), 2 * npx, "2 B read per pixel (uint8 pair)"),
+    }
+    out = {}
+    for name, (fn, nbytes, what) in calls.items():
+        ms = events_time(fn, steps, warmup, stream)
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "bytes": what, "GBs": nbytes / (ms / 1e3) / 1e9,
+                     "frac": nbytes / (ms / 1e3) / 1e9 / peak}
+    del Y, Yc, rec
+    return {"image": "1024 x 512^2 batch as one 512 x 524288 plane", "r": r, "peak_source": f"{kind} hbm_gbs",
+            "note": "each call includes its allocation of the output tensor (torch caching allocator)",
+            "calls": out}
 
 
 # ---------------------------------------------------------------- reference
@@ -704,10 +795,11 @@ def main():
                         "rdct_pipeline_create")
             rdct._check(lib.rdct_pipeline_set_mode(pipe, mode), "rdct_pipeline_set_mode")
             sse_h = (ctypes.c_double * wl.nimages)()
-            rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h), "rdct_pipeline_run")  # warm
+            rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h, None),
+                        "rdct_pipeline_run")  # warm
             t = time.perf_counter()
             for _ in range(args.e2e_steps):
-                rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h), "rdct_pipeline_run")
+                rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h, None), "rdct_pipeline_run")
             dt = (time.perf_counter() - t) / args.e2e_steps
             lib.rdct_pipeline_destroy(pipe)
             return dt, bool(np.allclose(np.array(sse_h[:]), wl.sse.cpu().numpy(), rtol=0, atol=0))
@@ -726,6 +818,27 @@ def main():
                                          "with kernels on three streams", "sse_matches_device_path": ok_s}}
         del bufs
 
+    if rank == 0 and args.workload == "video" and not args.no_extra:
+        k = min(args.steps, 20)
+        line["fused_r"] = fused_r_table(wl, (1, 4, 10, 16, 21, 32, 33, 40, 45, 55, 63, 64), k, 3, dev)
+        sub = argparse.Namespace(**{**vars(args), "steps": k, "warmup": 3})
+        u = bench_uneven(sub, dev)
+        line["uneven"] = {"workload": u["config"]["workload"], "value": u["value"], "unit": u["unit"],
+                          "ms_per_step": u["ms_per_step"], "frac": u["roofline"]["frac"],
+                          "achieved_GBs": u["roofline"]["achieved"], "planes": u["config"]["planes"],
+                          "samples_per_step": u["config"]["samples_per_step"], "tune": u["config"]["tune"],
+                          "kernels_per_step": u["gpu_launches"] // k,
+                          "per_plane_launches": u["per_plane_launches"],
+                          "batched_over_per_plane": u["batched_over_per_plane"],
+                          "sse_identical": u["sse_identical"], "quality": u["quality"]}
+        torch.cuda.empty_cache()
+        sw = bench_sweep(sub, dev)
+        line["sweep"] = {"workload": sw["config"]["workload"], "value": sw["value"], "unit": "Gsample/s",
+                         "ms_per_step": sw["ms_per_step"], "frac": sw["roofline"]["frac"],
+                         "per_r": {r: sw["per_r"][r] for r in ("1", "10", "16", "45") if r in sw["per_r"]},
+                         "uqi_subset_images": sw["uqi_kernel"]["uqi_subset_images"]}
+        line["steps_api"] = bench_steps(dev, k, 3)
+        torch.cuda.empty_cache()
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(dev, args.serving_requests)
     if rank == 0 and args.workload == "video" and not args.no_single:
@@ -733,9 +846,15 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, done, tt = cpu_oracle_rate(wl.cpu_planes(), args.r, args.cpu_seconds)
+        rate1, _, done1, tt1 = cpu_oracle_rate(wl.cpu_planes(), args.r, args.cpu_seconds / 2, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "cpu_model": cpu_model(),
                                 "sample": f"{done} samples = {100.0 * done / wl.samples:.0f}% of the same workload "
-                                          f"(its planes in order, up to {args.cpu_seconds:.0f} s), {tt:.1f} s of CPU time"}
+                                          f"(its planes in order, up to {args.cpu_seconds:.0f} s), {tt:.1f} s of "
+                                          f"wall time on {threads} threads",
+                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"{done1} samples (the first planes of the workload), "
+                                                            f"{tt1:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

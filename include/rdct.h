@@ -103,7 +103,10 @@ RDCT_API int32_t rdct_version(void);
  * (RDCT_ERR_CUDA).  Returns RDCT_ERR_TIMEOUT when a TMA-staged batch kernel
  * gave up waiting for a staged tile since the last check (its warp stopped
  * early, so that launch's outputs and errors are incomplete); the count is
- * reset by the check. */
+ * reset by the check.  A staged tile that never arrived in time may still
+ * land later in shared memory that another kernel then owns, so after a
+ * timeout treat the results of every launch that ran at the same time as
+ * suspect too. */
 RDCT_API rdct_status rdct_sync(rdct_stream stream);
 
 /* ------------------------------------------------------- the method's steps */
@@ -199,9 +202,14 @@ RDCT_API rdct_status rdct_uqi(const rdct_plane *ref, const rdct_out *rec, double
  * coefficients with the S scaling, inverse, squared error.  `out` may be
  * NULL (error only).  *sse (DEVICE double) receives the sum over pixels of
  * (Xhat - A)^2 for the unrounded reconstruction; for kind RDCT it is exact
- * (integer arithmetic, 576 * SSE accumulated in 64 bits). */
+ * (integer arithmetic, 576 * SSE accumulated in 64 bits).  sse_u8 (DEVICE
+ * double, 8-byte aligned, not the same slot as sse) may be NULL; otherwise it
+ * receives the sum of (q - A)^2 for the 8-bit reconstruction
+ * q = clamp(round(Xhat), 0, 255) that out->u8 holds (formed even when out or
+ * out->u8 is NULL), exact for both kinds.  PSNR of the 8-bit image =
+ * 10 log10(255^2 w h / sse_u8). */
 RDCT_API rdct_status rdct_fused(const rdct_plane *src, int32_t r, rdct_kind kind, const rdct_out *out, double *sse,
-                       rdct_stream stream);
+                       double *sse_u8, rdct_stream stream);
 
 /* The r sweep of Sec. 3 in one pass per plane: sse_by_r (DEVICE, [n][64]
  * doubles) receives, for each plane i and r = 1..64, the squared error of
@@ -221,7 +229,9 @@ RDCT_API rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind k
  * Limits: at most 2048 planes and 32768 chunks of 16 strips (about 1.07
  * Gpixel) per call, else RDCT_ERR_TOO_LARGE and nothing is enqueued.
  * The first call on a device looks up the array's device address (set-up,
- * once per device), so make it before any stream capture.  Every call shares
+ * once per device), so make it before any stream capture.  That address is
+ * kept for the life of the process: do not reset the device
+ * (cudaDeviceReset) while the library is loaded and this call is in use.  Every call shares
  * the array: calls that overlap on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller. */
 RDCT_API rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r,
@@ -264,13 +274,17 @@ RDCT_API rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs,
 /* Run the whole batch as one CUDA-graph launch: reset of the error slots,
  * one persistent kernel per r present (two where planes of that r take
  * different stagings), conversion of the slots to SSE.  The sequence is
- * captured on the first run with a given sse_per_image pointer and replayed
- * afterwards on `stream`.  sse_per_image: DEVICE, [nimages] doubles, 8-byte
- * aligned, overwritten. */
-RDCT_API rdct_status rdct_batch_run(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
+ * captured on the first run with given (sse_per_image, sse_u8_per_image)
+ * pointers and replayed afterwards on `stream`.  sse_per_image: DEVICE,
+ * [nimages] doubles, 8-byte aligned, overwritten (unrounded reconstruction).
+ * sse_u8_per_image: NULL, or another such array that receives each image's
+ * squared error of its 8-bit reconstruction (exact). */
+RDCT_API rdct_status rdct_batch_run(rdct_plan *plan, double *sse_per_image, double *sse_u8_per_image,
+                                    rdct_stream stream);
 /* Same work with one plain launch per plane (the baseline batching is
  * compared against). */
-RDCT_API rdct_status rdct_batch_run_per_plane(rdct_plan *plan, double *sse_per_image, rdct_stream stream);
+RDCT_API rdct_status rdct_batch_run_per_plane(rdct_plan *plan, double *sse_per_image, double *sse_u8_per_image,
+                                              rdct_stream stream);
 RDCT_API rdct_status rdct_batch_plan_get_tune(const rdct_plan *plan, rdct_tune *tune);
 /* Kernels one rdct_batch_run launches (host): one per non-empty group of
  * chunks (an r, or a register class for the scalar kernel, and a staging
@@ -303,9 +317,11 @@ typedef struct rdct_pipeline rdct_pipeline;
 RDCT_API rdct_status rdct_pipeline_create(int64_t device_budget_bytes, int32_t depth, rdct_pipeline **pipe);
 /* Process planes that live in host memory: copy in, run the fused path,
  * copy the uint8 reconstructions back, and write per-image SSE to the HOST
- * array sse_per_image[nimages].  Returns when everything is done. */
+ * array sse_per_image[nimages] and, unless sse_u8_per_image is NULL, the
+ * squared error of each image's 8-bit reconstruction to that HOST array.
+ * Returns when everything is done. */
 RDCT_API rdct_status rdct_pipeline_run(rdct_pipeline *pipe, const rdct_host_job *jobs, int32_t njobs, int32_t nimages,
-                              double *sse_per_image);
+                              double *sse_per_image, double *sse_u8_per_image);
 RDCT_API rdct_status rdct_pipeline_destroy(rdct_pipeline *pipe);
 
 /* How rdct_pipeline_run moves the planes:
@@ -346,6 +362,8 @@ typedef struct {
     double sse;        /* summed over planes, unrounded reconstruction */
     double mse, psnr;  /* over all samples of the image */
     double latency_us; /* submit -> completion */
+    double sse_u8;     /* the same for the 8-bit reconstruction that is returned */
+    double mse_u8, psnr_u8;
 } rdct_result;
 
 typedef struct {
@@ -353,6 +371,7 @@ typedef struct {
     double p50_us, p99_us, mean_us;
     double gpixels_per_s; /* samples processed / busy wall time */
     int64_t peak_resident_bytes;
+    double p999_us;
 } rdct_server_stats;
 
 typedef struct rdct_server rdct_server;

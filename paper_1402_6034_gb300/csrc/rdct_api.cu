@@ -151,9 +151,13 @@ int32_t rdct_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 rdct_status rdct_sync(rdct_stream stream) {
     RDCT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     RDCT_CUDA_TRY(cudaGetLastError());
-    const unsigned int t = take_tma_timeouts_r0() + take_tma_timeouts_r1() + take_tma_timeouts_r2() +
-                           take_tma_timeouts_r3() + take_tma_timeouts_r4() + take_tma_timeouts_r5() +
-                           take_tma_timeouts_r6() + take_tma_timeouts_r7();
+    unsigned int (*const takers[])() = {
+        take_tma_timeouts_r0,  take_tma_timeouts_r1,  take_tma_timeouts_r2,  take_tma_timeouts_r3,
+        take_tma_timeouts_r4,  take_tma_timeouts_r5,  take_tma_timeouts_r6,  take_tma_timeouts_r7,
+        take_tma_timeouts_r8,  take_tma_timeouts_r9,  take_tma_timeouts_r10, take_tma_timeouts_r11,
+        take_tma_timeouts_r12, take_tma_timeouts_r13, take_tma_timeouts_r14, take_tma_timeouts_r15};
+    unsigned int t = 0;
+    for (auto take : takers) t += take();
     if (t)
         return set_error(RDCT_ERR_TIMEOUT, "rdct_sync: " + std::to_string(t) +
                                                " TMA waits for a staged box ran out; the launches that hit them "
@@ -227,21 +231,27 @@ rdct_status rdct_mse_psnr(const rdct_plane *ref, const rdct_out *rec, double *ms
 }
 
 rdct_status rdct_fused(const rdct_plane *src, int32_t r, rdct_kind kind, const rdct_out *out, double *sse,
-                       rdct_stream stream) {
+                       double *sse_u8, rdct_stream stream) {
     rdct_status st = validate_plane(src, "rdct_fused");
     if (st) return st;
     if (r < 1 || r > 64) return set_error(RDCT_ERR_ARG, "rdct_fused: r must be in 1..64");
     if (kind != RDCT_KIND_RDCT && kind != RDCT_KIND_DCT) return set_error(RDCT_ERR_ARG, "rdct_fused: bad kind");
     if (!sse) return set_error(RDCT_ERR_ARG, "rdct_fused: null sse");
     if (reinterpret_cast<uintptr_t>(sse) % 8) return set_error(RDCT_ERR_ARG, "rdct_fused: sse must be 8-byte aligned");
+    if (reinterpret_cast<uintptr_t>(sse_u8) % 8)
+        return set_error(RDCT_ERR_ARG, "rdct_fused: sse_u8 must be 8-byte aligned");
+    if (sse_u8 == sse) return set_error(RDCT_ERR_ARG, "rdct_fused: sse and sse_u8 must be different slots");
     st = validate_out(out, src->w, src->h);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const JobDesc job = make_job(*src, out ? out->u8 : nullptr, out ? out->pitch : 0, out ? out->f32 : nullptr,
                                  out ? out->pitch_f32 : 0, r, 0, 1);
+    unsigned long long *acc8 = reinterpret_cast<unsigned long long *>(sse_u8);
     RDCT_CUDA_TRY(cudaMemsetAsync(sse, 0, sizeof(double), s));
-    RDCT_CUDA_TRY(launch_fused_single(job, (int)kind, sse, 0, 8, s));
-    if (kind == RDCT_KIND_RDCT) RDCT_CUDA_TRY(launch_sse576_to_double(sse, 1, s));
+    if (acc8) RDCT_CUDA_TRY(cudaMemsetAsync(acc8, 0, sizeof(double), s));
+    RDCT_CUDA_TRY(launch_fused_single(job, (int)kind, sse, acc8, 0, 8, s));
+    if (kind == RDCT_KIND_RDCT || acc8)
+        RDCT_CUDA_TRY(launch_sse576_to_double(kind == RDCT_KIND_RDCT ? sse : nullptr, 1, s, acc8));
     return RDCT_OK;
 }
 

@@ -39,11 +39,11 @@ struct rdct_plan {
     std::vector<unsigned char> maps; // two encoded tensor maps per job (zeros for jobs without TMA)
     std::vector<char> job_tma;       // per job: TMA staging
     unsigned char *d_maps = nullptr;
-    // graph cache: one executable per (sse pointer)
+    // graph cache: one executable for the last (sse, sse_u8) pointers
     std::mutex mu;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
-    double *exec_sse = nullptr;
+    double *exec_sse = nullptr, *exec_sse8 = nullptr;
 };
 
 namespace {
@@ -142,24 +142,34 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
 
 // memset -> one persistent kernel per non-empty group, in stream order (the
 // groups overlap only at their tails; running them as parallel graph branches
-// measured slower) -> in-place 576*SSE to SSE.
-cudaError_t enqueue_batch(rdct_plan *p, double *sse, cudaStream_t s) {
+// measured slower) -> in-place 576*SSE to SSE (and the 8-bit errors to double).
+cudaError_t enqueue_batch(rdct_plan *p, double *sse, double *sse8, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s);
+    if (e == cudaSuccess && sse8) e = cudaMemsetAsync(sse8, 0, (size_t)p->nimages * sizeof(double), s);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
+    unsigned long long *acc8 = reinterpret_cast<unsigned long long *>(sse8);
     bool first = true;
     for (int g = 0; g < 2 * kBatchGroups && e == cudaSuccess; ++g) {
         const int32_t b = p->group_begin[g], n = p->group_begin[g + 1] - b;
         if (n == 0) continue;
         if (g >= kBatchGroups)
-            e = launch_fused2_tma_batch(p->d_jobs, p->d_chunks + b, n, p->d_maps, acc, g - kBatchGroups + 1,
+            e = launch_fused2_tma_batch(p->d_jobs, p->d_chunks + b, n, p->d_maps, acc, acc8, g - kBatchGroups + 1,
                                         p->tune.ctas_per_sm, !first, s);
         else
-            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, g, p->tune.ctas_per_sm,
+            e = launch_fused_batch(p->d_jobs, p->d_chunks + b, n, acc, acc8, g, p->tune.ctas_per_sm,
                                    p->tune.warps_per_cta, p->tune.blocks_per_thread, !first, s);
         first = false;
     }
-    if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s);
+    if (e == cudaSuccess) e = launch_sse576_to_double(sse, p->nimages, s, sse8);
     return e;
+}
+
+rdct_status check_sse_args(const char *what, double *sse, double *sse8) {
+    if (!sse) return set_error(RDCT_ERR_ARG, std::string(what) + ": null argument");
+    if (reinterpret_cast<uintptr_t>(sse) % 8 || reinterpret_cast<uintptr_t>(sse8) % 8)
+        return set_error(RDCT_ERR_ARG, std::string(what) + ": misaligned sse");
+    if (sse8 == sse) return set_error(RDCT_ERR_ARG, std::string(what) + ": sse and sse_u8 must be different arrays");
+    return RDCT_OK;
 }
 
 std::mutex g_tune_mu;
@@ -235,18 +245,19 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     return RDCT_OK;
 }
 
-rdct_status rdct_batch_run(rdct_plan *p, double *sse, rdct_stream stream) {
-    if (!p || !sse) return set_error(RDCT_ERR_ARG, "rdct_batch_run: null argument");
-    if (reinterpret_cast<uintptr_t>(sse) % 8) return set_error(RDCT_ERR_ARG, "rdct_batch_run: misaligned sse");
+rdct_status rdct_batch_run(rdct_plan *p, double *sse, double *sse_u8, rdct_stream stream) {
+    if (!p) return set_error(RDCT_ERR_ARG, "rdct_batch_run: null argument");
+    rdct_status st = check_sse_args("rdct_batch_run", sse, sse_u8);
+    if (st) return st;
     std::lock_guard<std::mutex> lk(p->mu);
-    if (!p->exec || p->exec_sse != sse) {
+    if (!p->exec || p->exec_sse != sse || p->exec_sse8 != sse_u8) {
         if (p->exec) {
             cudaGraphExecDestroy(p->exec);
             p->exec = nullptr;
         }
         cudaGraph_t g = nullptr;
         RDCT_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_batch(p, sse, p->cap_stream);
+        cudaError_t e = enqueue_batch(p, sse, sse_u8, p->cap_stream);
         cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -260,20 +271,24 @@ rdct_status rdct_batch_run(rdct_plan *p, double *sse, rdct_stream stream) {
             return cuda_error(e, "rdct_batch_run: instantiate");
         }
         p->exec_sse = sse;
+        p->exec_sse8 = sse_u8;
     }
     RDCT_CUDA_TRY(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
     return RDCT_OK;
 }
 
-rdct_status rdct_batch_run_per_plane(rdct_plan *p, double *sse, rdct_stream stream) {
-    if (!p || !sse) return set_error(RDCT_ERR_ARG, "rdct_batch_run_per_plane: null argument");
-    if (reinterpret_cast<uintptr_t>(sse) % 8)
-        return set_error(RDCT_ERR_ARG, "rdct_batch_run_per_plane: misaligned sse");
+rdct_status rdct_batch_run_per_plane(rdct_plan *p, double *sse, double *sse_u8, rdct_stream stream) {
+    if (!p) return set_error(RDCT_ERR_ARG, "rdct_batch_run_per_plane: null argument");
+    rdct_status st = check_sse_args("rdct_batch_run_per_plane", sse, sse_u8);
+    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     RDCT_CUDA_TRY(cudaMemsetAsync(sse, 0, (size_t)p->nimages * sizeof(double), s));
+    if (sse_u8) RDCT_CUDA_TRY(cudaMemsetAsync(sse_u8, 0, (size_t)p->nimages * sizeof(double), s));
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(sse);
-    for (const JobDesc &j : p->jobs_pp) RDCT_CUDA_TRY(launch_fused_single(j, RDCT_KIND_RDCT, acc + j.image, 0, 8, s));
-    RDCT_CUDA_TRY(launch_sse576_to_double(sse, p->nimages, s));
+    unsigned long long *acc8 = reinterpret_cast<unsigned long long *>(sse_u8);
+    for (const JobDesc &j : p->jobs_pp)
+        RDCT_CUDA_TRY(launch_fused_single(j, RDCT_KIND_RDCT, acc + j.image, acc8 ? acc8 + j.image : nullptr, 0, 8, s));
+    RDCT_CUDA_TRY(launch_sse576_to_double(sse, p->nimages, s, sse_u8));
     return RDCT_OK;
 }
 
@@ -341,12 +356,12 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
             result = st;
             break;
         }
-        bool ok = rdct_batch_run(p, sse, s) == RDCT_OK;  // capture + warm-up
+        bool ok = rdct_batch_run(p, sse, nullptr, s) == RDCT_OK;  // capture + warm-up
         const int reps = 3;
         std::vector<float> times;
         for (int k = 0; k < reps && ok; ++k) {
             cudaEventRecord(e0, s);
-            ok = rdct_batch_run(p, sse, s) == RDCT_OK;
+            ok = rdct_batch_run(p, sse, nullptr, s) == RDCT_OK;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
             float ms = 0.0f;

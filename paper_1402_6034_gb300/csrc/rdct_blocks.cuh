@@ -160,11 +160,14 @@ __device__ __forceinline__ void forward_dct(const uint32_t w[16], float Y[8][8],
 // -------------------------------------------------------- fused block bodies
 
 // RDCT, retained zone = every anti-diagonal < D plus the ranks < r of diagonal D.
-// Returns 576 * SSE of the block (exact).
+// Returns 576 * SSE of the block (exact).  With OUT & 1, the 8-bit
+// reconstruction goes to dst when dst is not nullptr, and with e8 its squared
+// error against the block is added to s8 (sum a^2 - 2 sum q a + sum q^2 from
+// byte dot products: exact).
 template <int D, int OUT>
 __device__ __forceinline__ unsigned long long fused_block_rdct(const uint32_t w[16], int r, uint8_t *dst,
                                                                int64_t dpitch, int dalign, float *dstf,
-                                                               int64_t fpitch) {
+                                                               int64_t fpitch, bool e8, unsigned long long &s8) {
     unsigned sumsq = 0;
 #pragma unroll
     for (int k = 0; k < 16; ++k) sumsq = __dp4a(w[k], w[k], sumsq);
@@ -209,17 +212,22 @@ __device__ __forceinline__ unsigned long long fused_block_rdct(const uint32_t w[
         }
     });
     constexpr unsigned rm = row_mask(D);
+    unsigned qq = 0, qx = 0;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
         float E[8];
         c0t_inverse<rm>(U[n], E);
         if constexpr (OUT & 1) {
-            if (dst != nullptr) {  // uniform: batch planes may have no uint8 output
+            if (dst != nullptr || e8) {  // uniform: batch planes may have no uint8 output
                 int q[8];
 #pragma unroll
                 for (int m = 0; m < 8; ++m) q[m] = q_from_576(E[m]);
-                store_row_u8(dst + n * dpitch, dalign, pack4_sat(q[0], q[1], q[2], q[3]),
-                             pack4_sat(q[4], q[5], q[6], q[7]));
+                const uint32_t lo = pack4_sat(q[0], q[1], q[2], q[3]), hi = pack4_sat(q[4], q[5], q[6], q[7]);
+                if (e8) {
+                    qq = __dp4a(lo, lo, __dp4a(hi, hi, qq));
+                    qx = __dp4a(lo, w[2 * n], __dp4a(hi, w[2 * n + 1], qx));
+                }
+                if (dst != nullptr) store_row_u8(dst + n * dpitch, dalign, lo, hi);
             }
         }
         if constexpr (OUT & 2) {
@@ -229,13 +237,18 @@ __device__ __forceinline__ unsigned long long fused_block_rdct(const uint32_t w[
             store_row_f32(dstf + n * fpitch, v);
         }
     }
+    if constexpr (OUT & 1) {
+        if (e8) s8 += (unsigned long long)(sumsq + qq - 2u * qx);
+    }
     return 576ull * (unsigned long long)sumsq - (unsigned long long)kept;
 }
 
 // Exact DCT twin in FP32; returns the block's SSE (FP32 sum of 64 squares).
+// 8-bit output and its squared error (e8, exact integers) as for the RDCT.
 template <int D, int OUT>
 __device__ __forceinline__ float fused_block_dct(const uint32_t w[16], int r, const DctConsts &C, uint8_t *dst,
-                                                 int64_t dpitch, int dalign, float *dstf, int64_t fpitch) {
+                                                 int64_t dpitch, int dalign, float *dstf, int64_t fpitch, bool e8,
+                                                 unsigned long long &s8) {
     float A[8][8], Y[8][8];
     forward_dct(w, Y, A, C);
     static_for<0, 8>([&](auto ic) {
@@ -267,6 +280,7 @@ __device__ __forceinline__ float fused_block_dct(const uint32_t w[16], int r, co
     });
     constexpr unsigned rm = row_mask(D);
     float sse = 0.0f;
+    unsigned qq = 0, qx = 0;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
         float X[8];
@@ -277,26 +291,44 @@ __device__ __forceinline__ float fused_block_dct(const uint32_t w[16], int r, co
             sse = __fmaf_rn(e, e, sse);
         }
         if constexpr (OUT & 1) {
-            int q[8];
+            if (dst != nullptr || e8) {
+                int q[8];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) q[m] = q_of(X[m]);
-            store_row_u8(dst + n * dpitch, dalign, pack4_sat(q[0], q[1], q[2], q[3]),
-                         pack4_sat(q[4], q[5], q[6], q[7]));
+                for (int m = 0; m < 8; ++m) q[m] = q_of(X[m]);
+                const uint32_t lo = pack4_sat(q[0], q[1], q[2], q[3]), hi = pack4_sat(q[4], q[5], q[6], q[7]);
+                if (e8) {
+                    qq = __dp4a(lo, lo, __dp4a(hi, hi, qq));
+                    qx = __dp4a(lo, w[2 * n], __dp4a(hi, w[2 * n + 1], qx));
+                }
+                if (dst != nullptr) store_row_u8(dst + n * dpitch, dalign, lo, hi);
+            }
         }
         if constexpr (OUT & 2) store_row_f32(dstf + n * fpitch, X);
+    }
+    if constexpr (OUT & 1) {
+        if (e8) {
+            unsigned sumsq = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) sumsq = __dp4a(w[k], w[k], sumsq);
+            s8 += (unsigned long long)(sumsq + qq - 2u * qx);
+        }
     }
     return sse;
 }
 
 // ---------------------------------------------------------- fused kernels
 
+// acc: the plane's 576 * SSE (uint64, kind RDCT) or SSE (double, kind DCT);
+// acc8: the squared error of the 8-bit reconstruction (uint64) or nullptr.
 template <int D, int OUT, int KIND>
-__global__ void __launch_bounds__(256) fused_single_kernel(const JobDesc job, void *acc, const DctConsts C) {
+__global__ void __launch_bounds__(256) fused_single_kernel(const JobDesc job, void *acc, unsigned long long *acc8,
+                                                           const DctConsts C) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int nitems = job.nbh * job.segs;
-    unsigned long long s576 = 0;
+    const bool e8 = acc8 != nullptr;
+    unsigned long long s576 = 0, s8 = 0;
     double sd = 0.0;
     for (int it = warp; it < nitems; it += nwarps) {
         const int by = it / job.segs;
@@ -304,13 +336,14 @@ __global__ void __launch_bounds__(256) fused_single_kernel(const JobDesc job, vo
         if (bx < job.nbw) {
             uint32_t w[16];
             load_block(job.src + (int64_t)by * 8 * job.src_pitch + (int64_t)bx * 8, job.src_pitch, job.align, w);
-            uint8_t *dst = (OUT & 1) ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
+            uint8_t *dst = (OUT & 1) && job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
             float *dstf = (OUT & 2) ? job.dstf + (int64_t)by * 8 * job.dstf_pitch + (int64_t)bx * 8 : nullptr;
             if constexpr (KIND == RDCT_KIND_RDCT) {
-                s576 += fused_block_rdct<D, OUT>(w, job.r, dst, job.dst_pitch, job.dalign, dstf, job.dstf_pitch);
+                s576 += fused_block_rdct<D, OUT>(w, job.r, dst, job.dst_pitch, job.dalign, dstf, job.dstf_pitch, e8,
+                                                 s8);
             } else {
                 sd += (double)fused_block_dct<D, OUT>(w, job.r, C, dst, job.dst_pitch, job.dalign, dstf,
-                                                      job.dstf_pitch);
+                                                      job.dstf_pitch, e8, s8);
             }
         }
     }
@@ -321,10 +354,15 @@ __global__ void __launch_bounds__(256) fused_single_kernel(const JobDesc job, vo
         sd = warp_sum_f64(sd);
         if (lane == 0 && sd != 0.0) atomicAdd(reinterpret_cast<double *>(acc), sd);
     }
+    if (e8) {
+        s8 = warp_sum_u64(s8);
+        if (lane == 0 && s8) atomicAdd(acc8, s8);
+    }
 }
 
 template <int D, int OUT>
-__device__ __forceinline__ unsigned long long run_chunk_rdct(const JobDesc &job, const Chunk &ch, int lane) {
+__device__ __forceinline__ unsigned long long run_chunk_rdct(const JobDesc &job, const Chunk &ch, int lane, bool e8,
+                                                             unsigned long long &s8) {
     unsigned long long s576 = 0;
     for (int it = ch.item0; it < ch.item0 + ch.nitems; ++it) {
         const int by = it / job.segs;
@@ -332,8 +370,8 @@ __device__ __forceinline__ unsigned long long run_chunk_rdct(const JobDesc &job,
         if (bx < job.nbw) {
             uint32_t w[16];
             load_block(job.src + (int64_t)by * 8 * job.src_pitch + (int64_t)bx * 8, job.src_pitch, job.align, w);
-            uint8_t *dst = (OUT & 1) ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
-            s576 += fused_block_rdct<D, OUT>(w, job.r, dst, job.dst_pitch, job.dalign, nullptr, 0);
+            uint8_t *dst = (OUT & 1) && job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
+            s576 += fused_block_rdct<D, OUT>(w, job.r, dst, job.dst_pitch, job.dalign, nullptr, 0, e8, s8);
         }
     }
     return s576;
@@ -342,24 +380,30 @@ __device__ __forceinline__ unsigned long long run_chunk_rdct(const JobDesc &job,
 // Persistent kernel over a chunk table (uneven planes, per-plane r).  One
 // instantiation covers the anti-diagonal classes DLO..DHI so that classes with
 // very different register needs run in separate launches at their own
-// occupancy.
+// occupancy.  acc8: per-image squared error of the 8-bit reconstruction, or
+// nullptr.
 template <int OUT, int DLO, int DHI>
 __global__ void __launch_bounds__(256) fused_batch_kernel(const JobDesc *__restrict__ jobs,
                                                           const Chunk *__restrict__ chunks, int nchunks,
-                                                          unsigned long long *acc) {
+                                                          unsigned long long *acc, unsigned long long *acc8) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const bool e8 = acc8 != nullptr;
     for (int c = warp; c < nchunks; c += nwarps) {
         const Chunk ch = chunks[c];
         const JobDesc job = jobs[ch.job];
-        unsigned long long s = 0;
+        unsigned long long s = 0, s8 = 0;
         static_for<DLO, DHI + 1>([&](auto dc) {
             constexpr int d = decltype(dc)::value;
-            if (ch.cls == d) s = run_chunk_rdct<d, OUT>(job, ch, lane);
+            if (ch.cls == d) s = run_chunk_rdct<d, OUT>(job, ch, lane, e8, s8);
         });
         s = warp_sum_u64(s);
         if (lane == 0 && s) atomicAdd(&acc[job.image], s);
+        if (e8) {
+            s8 = warp_sum_u64(s8);
+            if (lane == 0 && s8) atomicAdd(&acc8[job.image], s8);
+        }
     }
 }
 
@@ -421,6 +465,6 @@ inline cudaError_t launch_staged(K kernel, int64_t units, int ctas_per_sm, int w
 // anti-diagonal class d selects the specialised kernel.
 template <int OUT, int KIND>
 cudaError_t launch_single_variant(int d, int64_t items, int ctas_per_sm, int warps, const JobDesc &job, void *acc,
-                                  const DctConsts &C, cudaStream_t s);
+                                  unsigned long long *acc8, const DctConsts &C, cudaStream_t s);
 
 }  // namespace rdct

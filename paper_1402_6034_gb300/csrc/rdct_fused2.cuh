@@ -22,7 +22,13 @@
 //     instructions;
 //   * error: 576 SSE = 576 sum x^2 - sum_kept W Y^2 (Parseval, the transform
 //     is orthogonal), with sum x^2 from dp4a and the kept energies summed
-//     per weight group in 32 bits: exact.
+//     per weight group in 32 bits: exact;
+//   * for r > 32 the same integers come from the coefficients that are
+//     dropped instead (576 Xhat = 576 A - C0^T (W o Y_dropped) C0 and
+//     576 SSE = sum_dropped W Y^2), so the work shrinks as r approaches 64,
+//     where the reconstruction is the block itself;
+//   * optionally the squared error of the 8-bit reconstruction, from byte dot
+//     products of the packed output with itself and with the pixels.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -101,6 +107,25 @@ __host__ __device__ constexpr unsigned kept_row_mask(int R) {
         if (kept_col_mask(R, j) != 0u) m |= 1u << j;
     return m;
 }
+// The same for the coefficients that are dropped (zigzag rank >= R).
+__host__ __device__ constexpr unsigned drop_col_mask(int R, int j) {
+    return ~kept_col_mask(R, j) & 0xFFu;
+}
+__host__ __device__ constexpr unsigned drop_row_mask(int R) {
+    unsigned m = 0u;
+    for (int j = 0; j < 8; ++j)
+        if (drop_col_mask(R, j) != 0u) m |= 1u << j;
+    return m;
+}
+
+// Where the reconstruction is built from the coefficients that are dropped
+// rather than from those that are kept.  With every coefficient kept the
+// scaled inverse returns the block exactly (C0^T (W o Y) C0 = 576 A, since
+// C0^T diag(g)^-1 C0 = I for C0 C0^T = diag(g), Sec. 2), so
+//   576 Xhat = 576 A - C0^T (W o Y_dropped) C0,
+//   576 SSE  = sum over the dropped positions of W Y^2   (Parseval),
+// the same integers as the kept form, in work that shrinks with 64 - r.
+__host__ __device__ constexpr bool drop_form(int R) { return R > 32; }
 
 __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][8]) {
     int R[8][8];
@@ -120,105 +145,204 @@ __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][
     }
 }
 
-// The two vertically adjacent blocks of a column pair at once, keeping
-// exactly the first R zigzag coefficients (R is a compile-time constant, so
-// the compiler drops every forward output, conversion and inverse term that
-// r never keeps).  The forward transform and the compression run per block
-// in int32, and from the compressed coefficients on every value is an f32x2
-// pair (block a, block b), so each inverse butterfly and each output scaling
-// serves both blocks.  wb is all zeros when the pair has only its upper block
-// (has_b false): a zero block contributes nothing to the error and is not
-// stored.  Returns 576 * SSE of the two blocks.  SMEM: dst is a shared-memory
-// staging box (row pitch dpitch, 8-byte aligned rows) that a TMA store writes
-// out, rather than the plane itself.
-template <int R, bool SMEM = false>
-__device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], uint8_t *dst,
-                                                          int64_t dpitch, int dalign, bool has_b) {
-    unsigned sumsq = 0;
+// Sum of squared pixels of both blocks (byte dot products).
+__device__ __forceinline__ unsigned pair_sumsq(const uint2 (&wa)[8], const uint2 (&wb)[8]) {
+    unsigned s = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        sumsq = __dp4a(wa[i].x, wa[i].x, sumsq);
-        sumsq = __dp4a(wa[i].y, wa[i].y, sumsq);
-        sumsq = __dp4a(wb[i].x, wb[i].x, sumsq);
-        sumsq = __dp4a(wb[i].y, wb[i].y, sumsq);
+        s = __dp4a(wa[i].x, wa[i].x, s);
+        s = __dp4a(wa[i].y, wa[i].y, s);
+        s = __dp4a(wb[i].x, wb[i].x, s);
+        s = __dp4a(wb[i].y, wb[i].y, s);
     }
-    int Ya[8][8], Yb[8][8];
-    forward_c0_int(wa, Ya);
-    forward_c0_int(wb, Yb);
-    // compression: Z = W Y on the retained coefficients, as f32x2 pairs in units of 2^-149
+    return s;
+}
+
+// Output of row n of both blocks from E = 576 Xhat (f32x2 pairs in units of
+// 2^-149): one f32x2 multiply by fl(1/576) leaves round(Xhat) in the bit
+// pattern, cvt.pack.sat clamps and packs.  The packed bytes q are stored
+// (dst may be nullptr: error only) and, with E8, their squared error against
+// the pixels is gathered as sum q^2 and sum q a (byte dot products), so that
+// sum (q - a)^2 = sum a^2 - 2 sum q a + sum q^2 is exact.
+template <bool SMEM, bool E8>
+__device__ __forceinline__ void emit_row(const f2 (&E)[8], int n, const uint2 &pa, const uint2 &pb, uint8_t *dst,
+                                         int64_t dpitch, int dalign, bool has_b, unsigned &qq, unsigned &qx) {
+    const f2 inv576 = f2_make(1.0f / 576.0f, 1.0f / 576.0f);
+    int qa[8], qb[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        float x, y;
+        f2_split(mul2(E[m], inv576), x, y);
+        qa[m] = __float_as_int(x);
+        qb[m] = __float_as_int(y);
+    }
+    const uint32_t a0 = pack4_sat(qa[0], qa[1], qa[2], qa[3]), a1 = pack4_sat(qa[4], qa[5], qa[6], qa[7]);
+    const uint32_t b0 = pack4_sat(qb[0], qb[1], qb[2], qb[3]), b1 = pack4_sat(qb[4], qb[5], qb[6], qb[7]);
+    if constexpr (E8) {
+        qq = __dp4a(a0, a0, qq);
+        qq = __dp4a(a1, a1, qq);
+        qq = __dp4a(b0, b0, qq);
+        qq = __dp4a(b1, b1, qq);
+        qx = __dp4a(a0, pa.x, qx);
+        qx = __dp4a(a1, pa.y, qx);
+        qx = __dp4a(b0, pb.x, qx);
+        qx = __dp4a(b1, pb.y, qx);
+    }
+    if (dst != nullptr) {
+        if constexpr (SMEM) {
+            *reinterpret_cast<uint2 *>(dst + n * dpitch) = make_uint2(a0, a1);
+            *reinterpret_cast<uint2 *>(dst + (8 + n) * dpitch) = make_uint2(b0, b1);
+        } else {
+            store_row_u8(dst + n * dpitch, dalign, a0, a1);
+            if (has_b) store_row_u8(dst + (8 + n) * dpitch, dalign, b0, b1);
+        }
+    }
+}
+
+// Z = s W Y (s = +1 or -1) for the coefficients of zone KEEP (kept: rank < R,
+// else dropped) of both blocks, as f32x2 pairs in units of 2^-149: one IMAD
+// builds the bit pattern of 1.5 * 2^23 + s W y, one FMA rescales it exactly.
+// Returns sum over the zone of W Y^2 for both blocks (per weight group in 32
+// bits: at most 576 sum a^2 per block in all, so no group overflows).
+template <int R, bool KEEP, int SIGN>
+__device__ __forceinline__ unsigned long long zone_to_z(const int (&Ya)[8][8], const int (&Yb)[8][8], f2 (&Z)[8][8]) {
     unsigned g2[6] = {0u, 0u, 0u, 0u, 0u, 0u};
     const f2 unit = f2_make(0x1p-149f, 0x1p-149f), bias = f2_make(-0x1.8p-126f, -0x1.8p-126f);
-    f2 Z[8][8];
     static_for<0, 8>([&](auto ic) {
         constexpr int i = decltype(ic)::value;
         static_for<0, 8>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
-            if constexpr (zz_rank(i, j) < R) {
+            if constexpr ((zz_rank(i, j) < R) == KEEP) {
                 const int ya = Ya[i][j], yb = Yb[i][j];
                 g2[weight_group(i, j)] += (unsigned)(ya * ya) + (unsigned)(yb * yb);
-                // bits of 1.5 * 2^23 + W y; the fma rescales by 2^-149 exactly
-                const int za = ya * weight(i, j) + 0x4B400000, zb = yb * weight(i, j) + 0x4B400000;
+                constexpr int sw = SIGN * weight(i, j);
+                const int za = ya * sw + 0x4B400000, zb = yb * sw + 0x4B400000;
                 Z[i][j] = fma2(f2_make(__int_as_float(za), __int_as_float(zb)), unit, bias);
             }
         });
     });
-    unsigned long long kept = 0;
+    unsigned long long e = 0;
 #pragma unroll
-    for (int g = 0; g < 6; ++g) kept += (unsigned long long)g2[g] * (unsigned)group_weight(g);
+    for (int g = 0; g < 6; ++g) e += (unsigned long long)g2[g] * (unsigned)group_weight(g);
+    return e;
+}
 
-    if (dst != nullptr) {
-        // inverse columns: U = C0^T Z
-        f2 U[8][8];
-        static_for<0, 8>([&](auto jc) {
-            constexpr int j = decltype(jc)::value;
-            constexpr unsigned m = kept_col_mask(R, j);
-            if constexpr (m != 0u) {
-                f2 in[8], out[8];
-                static_for<0, 8>([&](auto ic) {
-                    constexpr int i = decltype(ic)::value;
-                    if constexpr ((m >> i) & 1u) in[i] = Z[i][j];
-                    else in[i] = f2{0ull};
-                });
-                c0t_inverse<m>(in, out);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) U[i][j] = out[i];
-            }
-        });
-        // inverse rows, then round, clamp, pack, store (row n of both blocks)
-        constexpr unsigned rm = kept_row_mask(R);
-        const f2 inv576 = f2_make(1.0f / 576.0f, 1.0f / 576.0f);
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            f2 in[8], E[8];
-            static_for<0, 8>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                if constexpr ((rm >> j) & 1u) in[j] = U[n][j];
-                else in[j] = f2{0ull};
+// Column pass of the inverse over the zone's columns: U = C0^T Z.
+template <int R, bool KEEP>
+__device__ __forceinline__ void inverse_columns(const f2 (&Z)[8][8], f2 (&U)[8][8]) {
+    static_for<0, 8>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        constexpr unsigned m = KEEP ? kept_col_mask(R, j) : drop_col_mask(R, j);
+        if constexpr (m != 0u) {
+            f2 in[8], out[8];
+            static_for<0, 8>([&](auto ic) {
+                constexpr int i = decltype(ic)::value;
+                if constexpr ((m >> i) & 1u) in[i] = Z[i][j];
+                else in[i] = f2{0ull};
             });
-            c0t_inverse<rm>(in, E);
-            int qa[8], qb[8];
+            c0t_inverse<m>(in, out);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                float x, y;
-                f2_split(mul2(E[m], inv576), x, y);
-                qa[m] = __float_as_int(x);
-                qb[m] = __float_as_int(y);
-            }
-            if constexpr (SMEM) {
-                *reinterpret_cast<uint2 *>(dst + n * dpitch) =
-                    make_uint2(pack4_sat(qa[0], qa[1], qa[2], qa[3]), pack4_sat(qa[4], qa[5], qa[6], qa[7]));
-                *reinterpret_cast<uint2 *>(dst + (8 + n) * dpitch) =
-                    make_uint2(pack4_sat(qb[0], qb[1], qb[2], qb[3]), pack4_sat(qb[4], qb[5], qb[6], qb[7]));
-            } else {
-                store_row_u8(dst + n * dpitch, dalign, pack4_sat(qa[0], qa[1], qa[2], qa[3]),
-                             pack4_sat(qa[4], qa[5], qa[6], qa[7]));
-                if (has_b)
-                    store_row_u8(dst + (8 + n) * dpitch, dalign, pack4_sat(qb[0], qb[1], qb[2], qb[3]),
-                                 pack4_sat(qb[4], qb[5], qb[6], qb[7]));
+            for (int i = 0; i < 8; ++i) U[i][j] = out[i];
+        }
+    });
+}
+
+// Row n of the inverse's row pass: E = U[n] C0 over the zone's columns.
+template <unsigned RM>
+__device__ __forceinline__ void inverse_row(const f2 (&U)[8][8], int n, f2 (&E)[8]) {
+    f2 in[8];
+    static_for<0, 8>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        if constexpr ((RM >> j) & 1u) in[j] = U[n][j];
+        else in[j] = f2{0ull};
+    });
+    c0t_inverse<RM>(in, E);
+}
+
+// The two vertically adjacent blocks of a column pair at once, keeping
+// exactly the first R zigzag coefficients (R is a compile-time constant, so
+// the compiler drops every forward output, conversion and inverse term that
+// the form in use never needs).  The forward transform and the compression
+// run per block in int32, and from the compressed coefficients on every value
+// is an f32x2 pair (block a, block b), so each inverse butterfly and each
+// output scaling serves both blocks.  wb is all zeros when the pair has only
+// its upper block (has_b false): a zero block contributes nothing to either
+// error and is not stored.  Returns 576 * SSE of the two blocks (unrounded
+// reconstruction); with E8 also adds the squared error of the 8-bit
+// reconstruction to s8.  dst may be nullptr (errors only).  SMEM: dst is a
+// shared-memory staging box (row pitch dpitch, 8-byte aligned rows) that a
+// TMA store writes out, rather than the plane itself.  E8 is a compile-time
+// choice so that kernels without the 8-bit error keep their registers.
+template <int R, bool SMEM, bool E8>
+__device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], uint8_t *dst,
+                                                          int64_t dpitch, int dalign, bool has_b,
+                                                          unsigned long long &s8) {
+    const bool rec = E8 || dst != nullptr;
+    unsigned qq = 0, qx = 0, sumsq = 0;
+    if constexpr (R == 64) {
+        // nothing is dropped: the reconstruction is the block itself, both errors are 0
+        if (dst != nullptr) {
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                if constexpr (SMEM) {
+                    *reinterpret_cast<uint2 *>(dst + n * dpitch) = wa[n];
+                    *reinterpret_cast<uint2 *>(dst + (8 + n) * dpitch) = wb[n];
+                } else {
+                    store_row_u8(dst + n * dpitch, dalign, wa[n].x, wa[n].y);
+                    if (has_b) store_row_u8(dst + (8 + n) * dpitch, dalign, wb[n].x, wb[n].y);
+                }
             }
         }
+        return 0ull;
+    } else if constexpr (drop_form(R)) {
+        int Ya[8][8], Yb[8][8];
+        forward_c0_int(wa, Ya);
+        forward_c0_int(wb, Yb);
+        // Z = -W Y on the dropped coefficients, so that the inverse yields -D
+        f2 Z[8][8];
+        const unsigned long long dropped = zone_to_z<R, false, -1>(Ya, Yb, Z);
+        if (rec) {
+            if constexpr (E8) sumsq = pair_sumsq(wa, wb);
+            f2 U[8][8];
+            inverse_columns<R, false>(Z, U);
+            const f2 k576 = f2_make(576.0f, 576.0f);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                f2 E[8];
+                inverse_row<drop_row_mask(R)>(U, n, E);
+                // 576 Xhat = 576 A - D: a pixel as float bits is a * 2^-149 (exact,
+                // subnormal), and the FMA forms 576 a - D exactly
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const unsigned wA = m < 4 ? wa[n].x : wa[n].y, wB = m < 4 ? wb[n].x : wb[n].y;
+                    const f2 P = f2_make(__uint_as_float(byte_of(wA, m & 3)), __uint_as_float(byte_of(wB, m & 3)));
+                    E[m] = fma2(P, k576, E[m]);
+                }
+                emit_row<SMEM, E8>(E, n, wa[n], wb[n], dst, dpitch, dalign, has_b, qq, qx);
+            }
+            if constexpr (E8) s8 += (unsigned long long)(sumsq + qq - 2u * qx);
+        }
+        return dropped;
+    } else {
+        sumsq = pair_sumsq(wa, wb);
+        int Ya[8][8], Yb[8][8];
+        forward_c0_int(wa, Ya);
+        forward_c0_int(wb, Yb);
+        f2 Z[8][8];
+        const unsigned long long kept = zone_to_z<R, true, 1>(Ya, Yb, Z);
+        if (rec) {
+            f2 U[8][8];
+            inverse_columns<R, true>(Z, U);
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                f2 E[8];
+                inverse_row<kept_row_mask(R)>(U, n, E);
+                emit_row<SMEM, E8>(E, n, wa[n], wb[n], dst, dpitch, dalign, has_b, qq, qx);
+            }
+            if constexpr (E8) s8 += (unsigned long long)(sumsq + qq - 2u * qx);
+        }
+        return 576ull * (unsigned long long)sumsq - kept;
     }
-    return 576ull * (unsigned long long)sumsq - kept;
 }
 
 // ------------------------------------------------------------------ kernel
@@ -256,6 +380,7 @@ struct Fused2Args {
     int32_t nchunks;
     int32_t chunk_items;       // single: items per virtual chunk
     unsigned long long *acc;   // batch: per-image 576*SSE; single: one slot
+    unsigned long long *acc8;  // same slots for the squared error of the 8-bit reconstruction, or nullptr
     JobDesc single;            // single-plane job (by value)
 };
 
@@ -348,8 +473,9 @@ __device__ __forceinline__ void fetch_strip(const JobDesc &job, int rp, int bx, 
 // Persistent fused kernel: each lane owns kVRows vertically adjacent blocks of
 // every strip its warp visits; strips stream through a double-buffered
 // per-thread cp.async ring.  CLO..CHI are the launch classes compiled in
-// (class r - 1 keeps r coefficients; one class per launch).
-template <int CLO, int CHI, bool SINGLE, int THREADS, int MINB>
+// (class r - 1 keeps r coefficients; one class per launch).  E8: also the
+// squared error of the 8-bit reconstruction (into a.acc8).
+template <int CLO, int CHI, bool SINGLE, int THREADS, int MINB, bool E8>
 __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args a) {
     __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
     // The next launch of a batch (another r) may start as CTAs of this one
@@ -372,7 +498,7 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
             cp_async_commit();
         }
     }
-    unsigned long long s576 = 0;
+    unsigned long long s576 = 0, s8 = 0;
     int stage = 0;
     while (cc.c < a.nchunks) {
         cp_async_wait<kStages - 2>();
@@ -401,17 +527,22 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_kernel(const Fused2Args 
             }
             static_for<CLO, CHI + 1>([&](auto cc_) {
                 constexpr int c = decltype(cc_)::value;
-                if (cc.cls == c) s576 += fused2_pair<c + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
+                if (cc.cls == c) s576 += fused2_pair<c + 1, false, E8>(wa, wb, dst, job.dst_pitch, job.dalign, has_b, s8);
             });
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
         const int img = job.image;
         const int cprev = cc.c;
         cursor_next<SINGLE>(a, cc, nwarps, lane);
-        if (cc.c != cprev) {  // end of a chunk: one atomic per warp
+        if (cc.c != cprev) {  // end of a chunk: one atomic per warp (and error)
             const unsigned long long t = warp_sum_u64(s576);
             if (lane == 0 && t) atomicAdd(SINGLE ? a.acc : a.acc + img, t);
             s576 = 0;
+            if constexpr (E8) {
+                const unsigned long long t8 = warp_sum_u64(s8);
+                if (lane == 0 && t8) atomicAdd(SINGLE ? a.acc8 : a.acc8 + img, t8);
+                s8 = 0;
+            }
         }
     }
     cp_async_wait<0>();
@@ -438,6 +569,7 @@ struct TmaArgs {
     const unsigned char *maps;  // per job: the source plane's tensor map, then the destination's
     int32_t nchunks;
     unsigned long long *acc;    // per-image 576 * SSE
+    unsigned long long *acc8;   // per-image squared error of the 8-bit reconstruction, or nullptr
 };
 
 __device__ unsigned int g_tma_timeouts = 0;
@@ -479,8 +611,8 @@ __device__ __forceinline__ void tma_request(const unsigned char *map, uint32_t d
 }
 
 // TSTORE: the reconstruction goes out through the box with TMA stores, else
-// with per-thread stores straight from registers.
-template <int CLS, int THREADS, int MINB, bool TSTORE>
+// with per-thread stores straight from registers.  E8 as for fused2_kernel.
+template <int CLS, int THREADS, int MINB, bool TSTORE, bool E8>
 __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs a) {
     constexpr int WARPS = THREADS / 32;
     __shared__ __align__(128) unsigned char boxes[WARPS * kStages * kTmaBoxBytes];
@@ -536,7 +668,7 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
     Chunk cch = ch;
     advance();
     uint32_t phase = 0u;           // bit st: parity of stage st's next completion
-    unsigned long long s576 = 0;
+    unsigned long long s576 = 0, s8 = 0;
     int stage = 0;
     while (true) {
         const bool more = c < a.nchunks;
@@ -567,10 +699,11 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
             const bool has_b = by + 1 < job.nbh;
             if constexpr (TSTORE) {
                 // the reconstruction replaces the pixels in the box (each lane its own columns)
-                s576 += fused2_pair<CLS + 1, true>(wa, wb, store ? box + lane * 8 : nullptr, kTmaBoxW, 8, has_b);
+                s576 += fused2_pair<CLS + 1, true, E8>(wa, wb, store ? box + lane * 8 : nullptr, kTmaBoxW, 8, has_b,
+                                                       s8);
             } else {
                 uint8_t *dst = job.dst ? job.dst + (int64_t)by * 8 * job.dst_pitch + (int64_t)bx * 8 : nullptr;
-                s576 += fused2_pair<CLS + 1>(wa, wb, dst, job.dst_pitch, job.dalign, has_b);
+                s576 += fused2_pair<CLS + 1, false, E8>(wa, wb, dst, job.dst_pitch, job.dalign, has_b, s8);
             }
         }
         if (store) {  // one TMA store of the box; columns and rows outside the plane are dropped
@@ -580,10 +713,15 @@ __global__ void __launch_bounds__(THREADS, MINB) fused2_tma_kernel(const TmaArgs
                 tma_store(a.maps + (int64_t)cch.job * 2 * kTensorMapBytes + kTensorMapBytes,
                           (uint32_t)__cvta_generic_to_shared(box), cseg * kTmaBoxW, crp * kTmaBoxH);
         }
-        if (!more || c != cur_c) {  // the item closed its chunk: one atomic per warp and chunk
+        if (!more || c != cur_c) {  // the item closed its chunk: one atomic per warp and chunk (and error)
             const unsigned long long t = warp_sum_u64(s576);
             if (lane == 0 && t) atomicAdd(a.acc + job.image, t);
             s576 = 0;
+            if constexpr (E8) {
+                const unsigned long long t8 = warp_sum_u64(s8);
+                if (lane == 0 && t8) atomicAdd(a.acc8 + job.image, t8);
+                s8 = 0;
+            }
         }
         if (!more) break;
         cur_c = c;
@@ -608,8 +746,12 @@ template <int R>
 cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap, cudaStream_t s) {
     constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
     constexpr bool TS = tma_store_pays(R);
-    return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
-                         (T / 32) * kStages * kTmaBoxBytes, overlap, s, a);
+    constexpr int smem = (T / 32) * kStages * kTmaBoxBytes;
+    if (a.acc8 != nullptr)
+        return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS, true>, a.nchunks, ctas_per_sm, T / 32,
+                             kFused2MaxCtas, smem, overlap, s, a);
+    return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS, false>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
+                         smem, overlap, s, a);
 }
 
 // Launch for exactly r = R retained coefficients: single-plane (a.single) or
@@ -619,11 +761,16 @@ cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap,
 template <int R>
 cudaError_t launch_fused2_r(const Fused2Args &a, bool single, int ctas_per_sm, bool overlap, cudaStream_t s) {
     constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
+    const bool e8 = a.acc8 != nullptr;
     if (single)
-        return launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB>, a.nchunks, ctas_per_sm, T / 32,
-                             kFused2MaxCtas, kFused2Smem, false, s, a);
-    return launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
-                         kFused2Smem, overlap, s, a);
+        return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB, true>, a.nchunks, ctas_per_sm, T / 32,
+                                  kFused2MaxCtas, kFused2Smem, false, s, a)
+                  : launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB, false>, a.nchunks, ctas_per_sm, T / 32,
+                                  kFused2MaxCtas, kFused2Smem, false, s, a);
+    return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB, true>, a.nchunks, ctas_per_sm, T / 32,
+                              kFused2MaxCtas, kFused2Smem, overlap, s, a)
+              : launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB, false>, a.nchunks, ctas_per_sm, T / 32,
+                              kFused2MaxCtas, kFused2Smem, overlap, s, a);
 }
 
 }  // namespace rdct

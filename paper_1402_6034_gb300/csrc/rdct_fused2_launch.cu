@@ -282,8 +282,8 @@ cudaError_t launch_fused2_tma_any(int r, const TmaArgs &a, int ctas_per_sm, bool
 }  // namespace
 
 cudaError_t launch_fused2_tma_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks,
-                                    const unsigned char *maps, unsigned long long *acc, int r, int ctas_per_sm,
-                                    bool overlap, cudaStream_t s) {
+                                    const unsigned char *maps, unsigned long long *acc, unsigned long long *acc8,
+                                    int r, int ctas_per_sm, bool overlap, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
     TmaArgs a{};
     a.jobs = jobs;
@@ -291,11 +291,12 @@ cudaError_t launch_fused2_tma_batch(const JobDesc *jobs, const Chunk *chunks, in
     a.maps = maps;
     a.nchunks = nchunks;
     a.acc = acc;
+    a.acc8 = acc8;
     return launch_fused2_tma_any(r, a, ctas_per_sm, overlap, s);
 }
 
-cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, int ctas_per_sm, int chunk_items,
-                                 cudaStream_t s) {
+cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, unsigned long long *acc8,
+                                 int ctas_per_sm, int chunk_items, cudaStream_t s) {
     Fused2Args a{};
     a.single = job;
     const int64_t items = fused_items_of(job);
@@ -306,18 +307,20 @@ cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, in
     a.chunk_items = chunk_items;
     a.nchunks = (int32_t)((items + a.chunk_items - 1) / a.chunk_items);
     a.acc = acc;
+    a.acc8 = acc8;
     if (a.nchunks == 0) return cudaSuccess;
     return launch_fused2_any(job.r, a, true, ctas_per_sm, false, s);
 }
 
 cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
-                                int r, int ctas_per_sm, bool overlap, cudaStream_t s) {
+                                unsigned long long *acc8, int r, int ctas_per_sm, bool overlap, cudaStream_t s) {
     if (nchunks <= 0) return cudaSuccess;
     Fused2Args a{};
     a.jobs = jobs;
     a.chunks = chunks;
     a.nchunks = nchunks;
     a.acc = acc;
+    a.acc8 = acc8;
     return launch_fused2_any(r, a, false, ctas_per_sm, overlap, s);
 }
 

@@ -1,5 +1,6 @@
-// Instantiations of the fused kernel for r = 1..8 (eight per translation
-// unit so that the 64 specialisations compile in parallel).
+// Instantiations of the fused kernel for r = 1..4 (four per translation unit
+// so that the 64 specialisations, each with and without the 8-bit error, compile
+// in parallel).
 #include "rdct_fused2.cuh"
 
 namespace rdct {
@@ -7,18 +8,10 @@ template cudaError_t launch_fused2_r<1>(const Fused2Args &, bool, int, bool, cud
 template cudaError_t launch_fused2_r<2>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<3>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_r<4>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<5>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<6>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<7>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<8>(const Fused2Args &, bool, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_tma_r<1>(const TmaArgs &, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_tma_r<2>(const TmaArgs &, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_tma_r<3>(const TmaArgs &, int, bool, cudaStream_t);
 template cudaError_t launch_fused2_tma_r<4>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<5>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<6>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<7>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<8>(const TmaArgs &, int, bool, cudaStream_t);
 
 // Reads and clears this translation unit's count of TMA waits that ran out
 // (each translation unit holds its own copy of the counter).

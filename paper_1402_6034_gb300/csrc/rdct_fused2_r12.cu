@@ -1,0 +1,30 @@
+// Instantiations of the fused kernel for r = 49..52 (four per translation unit
+// so that the 64 specialisations, each with and without the 8-bit error, compile
+// in parallel).
+#include "rdct_fused2.cuh"
+
+namespace rdct {
+template cudaError_t launch_fused2_r<49>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<50>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<51>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<52>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<49>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<50>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<51>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<52>(const TmaArgs &, int, bool, cudaStream_t);
+
+// Reads and clears this translation unit's count of TMA waits that ran out
+// (each translation unit holds its own copy of the counter).
+unsigned int take_tma_timeouts_r12() {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tma_timeouts, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (v) {
+        const unsigned int zero = 0;
+        cudaMemcpyToSymbol(g_tma_timeouts, &zero, sizeof(zero));
+    }
+    return v;
+}
+}  // namespace rdct

@@ -1,24 +1,17 @@
-// Instantiations of the fused kernel for r = 17..24 (eight per translation
-// unit so that the 64 specialisations compile in parallel).
+// Instantiations of the fused kernel for r = 9..12 (four per translation unit
+// so that the 64 specialisations, each with and without the 8-bit error, compile
+// in parallel).
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<17>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<18>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<19>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<20>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<21>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<22>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<23>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<24>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<17>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<18>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<19>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<20>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<21>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<22>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<23>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<24>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<9>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<10>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<11>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<12>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<9>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<10>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<11>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<12>(const TmaArgs &, int, bool, cudaStream_t);
 
 // Reads and clears this translation unit's count of TMA waits that ran out
 // (each translation unit holds its own copy of the counter).

@@ -1,24 +1,17 @@
-// Instantiations of the fused kernel for r = 33..40 (eight per translation
-// unit so that the 64 specialisations compile in parallel).
+// Instantiations of the fused kernel for r = 17..20 (four per translation unit
+// so that the 64 specialisations, each with and without the 8-bit error, compile
+// in parallel).
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<33>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<34>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<35>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<36>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<37>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<38>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<39>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<40>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<33>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<34>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<35>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<36>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<37>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<38>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<39>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<40>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<17>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<18>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<19>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<20>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<17>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<18>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<19>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<20>(const TmaArgs &, int, bool, cudaStream_t);
 
 // Reads and clears this translation unit's count of TMA waits that ran out
 // (each translation unit holds its own copy of the counter).

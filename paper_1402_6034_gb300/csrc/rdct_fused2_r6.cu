@@ -1,24 +1,17 @@
-// Instantiations of the fused kernel for r = 49..56 (eight per translation
-// unit so that the 64 specialisations compile in parallel).
+// Instantiations of the fused kernel for r = 25..28 (four per translation unit
+// so that the 64 specialisations, each with and without the 8-bit error, compile
+// in parallel).
 #include "rdct_fused2.cuh"
 
 namespace rdct {
-template cudaError_t launch_fused2_r<49>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<50>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<51>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<52>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<53>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<54>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<55>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_r<56>(const Fused2Args &, bool, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<49>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<50>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<51>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<52>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<53>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<54>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<55>(const TmaArgs &, int, bool, cudaStream_t);
-template cudaError_t launch_fused2_tma_r<56>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<25>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<26>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<27>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_r<28>(const Fused2Args &, bool, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<25>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<26>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<27>(const TmaArgs &, int, bool, cudaStream_t);
+template cudaError_t launch_fused2_tma_r<28>(const TmaArgs &, int, bool, cudaStream_t);
 
 // Reads and clears this translation unit's count of TMA waits that ran out
 // (each translation unit holds its own copy of the counter).

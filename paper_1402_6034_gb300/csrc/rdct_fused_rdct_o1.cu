@@ -4,5 +4,6 @@
 
 namespace rdct {
 template cudaError_t launch_single_variant<1, 0>(int, int64_t, int, int, const JobDesc &, void *,
+                                                      unsigned long long *,
                                                       const DctConsts &, cudaStream_t);
 }  // namespace rdct

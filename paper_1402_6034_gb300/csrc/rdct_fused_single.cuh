@@ -9,11 +9,11 @@ namespace rdct {
 
 template <int OUT, int KIND>
 cudaError_t launch_single_variant(int d, int64_t items, int ctas_per_sm, int warps, const JobDesc &job, void *acc,
-                                  const DctConsts &C, cudaStream_t s) {
+                                  unsigned long long *acc8, const DctConsts &C, cudaStream_t s) {
     switch (d) {
 #define RDCT_LCASE(dd)                                                                                      \
     case dd:                                                                                                \
-        launch_persistent(fused_single_kernel<dd, OUT, KIND>, items, ctas_per_sm, warps, s, job, acc, C); \
+        launch_persistent(fused_single_kernel<dd, OUT, KIND>, items, ctas_per_sm, warps, s, job, acc, acc8, C); \
         break;
         RDCT_LCASE(0) RDCT_LCASE(1) RDCT_LCASE(2) RDCT_LCASE(3) RDCT_LCASE(4) RDCT_LCASE(5) RDCT_LCASE(6)
         RDCT_LCASE(7) RDCT_LCASE(8) RDCT_LCASE(9) RDCT_LCASE(10) RDCT_LCASE(11) RDCT_LCASE(12) RDCT_LCASE(13)

@@ -94,12 +94,17 @@ cudaError_t launch_sse(const JobDesc &ref, const uint8_t *rec_u8, int64_t rec_pi
 cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double *acc_f64, int use_u64,
                                 double nsamples, double *mse, double *psnr, cudaStream_t s);
 // Fused path for one job: acc is the caller's SSE slot (zeroed by the caller),
-// used as uint64 576*SSE for kind RDCT and as double SSE for kind DCT.
-cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, int ctas_per_sm, int warps, cudaStream_t s);
+// used as uint64 576*SSE for kind RDCT and as double SSE for kind DCT; acc8
+// (uint64, zeroed by the caller, or nullptr) receives the squared error of the
+// 8-bit reconstruction, which is then formed even when job.dst is nullptr.
+cudaError_t launch_fused_single(const JobDesc &job, int kind, void *acc, unsigned long long *acc8, int ctas_per_sm,
+                                int warps, cudaStream_t s);
 // Persistent batch kernels.  Chunks are grouped: with blocks_per_thread 2
 // one group per r (64 groups, a kernel specialised for each r), with
 // blocks_per_thread 1 one group per register class (3 groups).
-// acc_u64[image] += 576 * SSE.  ctas_per_sm <= 0 uses the occupancy limit.
+// acc_u64[image] += 576 * SSE, and acc8[image] (unless nullptr) += the
+// squared error of the 8-bit reconstruction.  ctas_per_sm <= 0 uses the
+// occupancy limit.
 constexpr int kBatchGroups = 64;
 int fused_class_of(int r, int blocks_per_thread);
 int batch_group_of_class(int cls, int blocks_per_thread);
@@ -109,20 +114,20 @@ int batch_group_of_class(int cls, int blocks_per_thread);
 // launch of the same batch in the stream drains (programmatic dependent
 // launch); pass false for the first launch of a batch.
 cudaError_t launch_fused_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc_u64,
-                               int group, int ctas_per_sm, int warps, int blocks_per_thread, bool overlap,
-                               cudaStream_t s);
+                               unsigned long long *acc8, int group, int ctas_per_sm, int warps, int blocks_per_thread,
+                               bool overlap, cudaStream_t s);
 // The fused kernel for sm_103a issue rates (dp4a row pass, f32x2 inverse,
 // cp.async ring): uint8 output or error only, any alignment.
-cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, int ctas_per_sm, int chunk_items,
-                                 cudaStream_t s);
+cudaError_t launch_fused2_single(const JobDesc &job, unsigned long long *acc, unsigned long long *acc8,
+                                 int ctas_per_sm, int chunk_items, cudaStream_t s);
 cudaError_t launch_fused2_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, unsigned long long *acc,
-                                int r, int ctas_per_sm, bool overlap, cudaStream_t s);
+                                unsigned long long *acc8, int r, int ctas_per_sm, bool overlap, cudaStream_t s);
 // The same kernel with TMA loads and stores, for batch tables whose items are
 // row pair x 32-column segments (tma_items_of) and whose planes have encoded
 // tensor maps (two of kTensorMapBytes each per plane, see tma_encode_plane).
 cudaError_t launch_fused2_tma_batch(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks,
-                                    const unsigned char *maps, unsigned long long *acc, int r, int ctas_per_sm,
-                                    bool overlap, cudaStream_t s);
+                                    const unsigned char *maps, unsigned long long *acc, unsigned long long *acc8,
+                                    int r, int ctas_per_sm, bool overlap, cudaStream_t s);
 inline int32_t tma_items_of(const JobDesc &j) { return ((j.nbh + 1) / 2) * ((j.nbw + 31) / 32); }
 constexpr int kTensorMapBytes = 128;  // one encoded 2-D tensor map per plane (64-byte aligned in the table)
 // TMA staging needs the source plane and the reconstruction (if any) to start
@@ -143,8 +148,18 @@ unsigned int take_tma_timeouts_r4();
 unsigned int take_tma_timeouts_r5();
 unsigned int take_tma_timeouts_r6();
 unsigned int take_tma_timeouts_r7();
-// In-place conversion of n uint64 576*SSE slots to double SSE.
-cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s);
+unsigned int take_tma_timeouts_r8();
+unsigned int take_tma_timeouts_r9();
+unsigned int take_tma_timeouts_r10();
+unsigned int take_tma_timeouts_r11();
+unsigned int take_tma_timeouts_r12();
+unsigned int take_tma_timeouts_r13();
+unsigned int take_tma_timeouts_r14();
+unsigned int take_tma_timeouts_r15();
+// In-place conversion of n uint64 576*SSE slots to double SSE (slots not
+// nullptr), and of n uint64 squared errors of 8-bit reconstructions in slots8
+// (if not nullptr) to double.
+cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s, void *slots8 = nullptr);
 // Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are
 // runs of at most kSweepChunkStrips strips of kFusedVRows block rows.
 constexpr int kSweepChunkStrips = 8;

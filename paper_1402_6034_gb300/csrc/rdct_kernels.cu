@@ -18,11 +18,19 @@
 
 namespace rdct {
 
-__global__ void sse576_to_double_kernel(void *slots, int32_t n) {
+// In place: uint64 576 * SSE -> double SSE (slots not nullptr), and uint64
+// squared errors of 8-bit reconstructions -> double (slots8 not nullptr).
+__global__ void sse576_to_double_kernel(void *slots, void *slots8, int32_t n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const unsigned long long u = reinterpret_cast<unsigned long long *>(slots)[i];
-        reinterpret_cast<double *>(slots)[i] = (double)u / 576.0;
+        if (slots != nullptr) {
+            const unsigned long long u = reinterpret_cast<unsigned long long *>(slots)[i];
+            reinterpret_cast<double *>(slots)[i] = (double)u / 576.0;
+        }
+        if (slots8 != nullptr) {
+            const unsigned long long v = reinterpret_cast<unsigned long long *>(slots8)[i];
+            reinterpret_cast<double *>(slots8)[i] = (double)v;
+        }
     }
 }
 
@@ -307,9 +315,9 @@ cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s) {
+cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s, void *slots8) {
     if (n <= 0) return cudaSuccess;
-    sse576_to_double_kernel<<<(n + 255) / 256, 256, 0, s>>>(slots, n);
+    sse576_to_double_kernel<<<(n + 255) / 256, 256, 0, s>>>(slots, slots8, n);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ struct rdct_pipeline {
     int64_t slot_bytes = 0;  // per direction
     std::vector<Slot> slots;
     cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
-    unsigned long long *d_acc = nullptr;
+    unsigned long long *d_acc = nullptr;  // [2 * acc_cap]: 576 * SSE per image, then the 8-bit errors
     int32_t acc_cap = 0;
 };
 
@@ -124,7 +124,8 @@ static bool device_addressable(const void *p, int64_t bytes) {
 // the reconstructions back to host memory over the host link, with no
 // staging copies; only the job and chunk tables and the per-image errors
 // cross the link as copies.
-static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32_t njobs) {
+static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32_t njobs,
+                              unsigned long long *acc8) {
     std::vector<JobDesc> jd;
     std::vector<Chunk> cd;
     jd.reserve(njobs);
@@ -151,7 +152,7 @@ static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32
         int32_t end = begin;
         while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
         if (end > begin) {
-            RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2,
+            RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, acc8, c, 0, 4, 2,
                                              begin > 0, p->comp));
         }
         begin = end;
@@ -160,14 +161,20 @@ static rdct_status run_direct(rdct_pipeline *p, const rdct_host_job *jobs, int32
 }
 
 // Wait for the run and hand the per-image errors to the host.
-static rdct_status finish_run(rdct_pipeline *p, int32_t nimages, double *sse_per_image) {
+static rdct_status finish_run(rdct_pipeline *p, int32_t nimages, double *sse_per_image, double *sse_u8) {
     RDCT_CUDA_TRY(cudaStreamSynchronize(p->comp));
     RDCT_CUDA_TRY(cudaStreamSynchronize(p->d2h));
     if (nimages > 0) {
-        std::vector<unsigned long long> acc(nimages);
+        std::vector<unsigned long long> acc(2 * (size_t)nimages);
         RDCT_CUDA_TRY(cudaMemcpy(acc.data(), p->d_acc, (size_t)nimages * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost));
-        for (int32_t i = 0; i < nimages; ++i) sse_per_image[i] = (double)acc[i] / 576.0;
+        if (sse_u8)
+            RDCT_CUDA_TRY(cudaMemcpy(acc.data() + nimages, p->d_acc + p->acc_cap,
+                                     (size_t)nimages * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        for (int32_t i = 0; i < nimages; ++i) {
+            sse_per_image[i] = (double)acc[i] / 576.0;
+            if (sse_u8) sse_u8[i] = (double)acc[nimages + i];
+        }
     }
     return RDCT_OK;
 }
@@ -214,7 +221,7 @@ rdct_status rdct_pipeline_create(int64_t device_budget_bytes, int32_t depth, rdc
 }
 
 rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32_t njobs, int32_t nimages,
-                              double *sse_per_image) {
+                              double *sse_per_image, double *sse_u8_per_image) {
     if (!p || (!jobs && njobs > 0) || njobs < 0 || nimages < 0 || (!sse_per_image && nimages > 0))
         return set_error(RDCT_ERR_ARG, "rdct_pipeline_run: null or negative argument");
     for (int32_t i = 0; i < njobs; ++i) {
@@ -230,11 +237,14 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
     if (nimages > p->acc_cap) {
         cudaFree(p->d_acc);
         p->d_acc = nullptr;
-        if (cudaMalloc(&p->d_acc, (size_t)nimages * sizeof(unsigned long long)) != cudaSuccess)
+        p->acc_cap = 0;
+        if (cudaMalloc(&p->d_acc, 2 * (size_t)nimages * sizeof(unsigned long long)) != cudaSuccess)
             return set_error(RDCT_ERR_OOM, "rdct_pipeline_run: accumulator allocation failed");
         p->acc_cap = nimages;
     }
-    if (nimages > 0) RDCT_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, (size_t)nimages * sizeof(unsigned long long), p->comp));
+    if (nimages > 0)
+        RDCT_CUDA_TRY(cudaMemsetAsync(p->d_acc, 0, 2 * (size_t)p->acc_cap * sizeof(unsigned long long), p->comp));
+    unsigned long long *acc8 = sse_u8_per_image ? p->d_acc + p->acc_cap : nullptr;
 
     bool direct = p->mode != RDCT_PIPELINE_STAGED;
     for (int32_t i = 0; i < njobs && direct; ++i) {
@@ -245,9 +255,9 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
     if (p->mode == RDCT_PIPELINE_DIRECT && !direct)
         return set_error(RDCT_ERR_ARG, "rdct_pipeline_run: direct mode needs pinned host planes");
     if (direct) {
-        rdct_status st = run_direct(p, jobs, njobs);
+        rdct_status st = run_direct(p, jobs, njobs, acc8);
         if (st) return st;
-        return finish_run(p, nimages, sse_per_image);
+        return finish_run(p, nimages, sse_per_image, sse_u8_per_image);
     }
 
     // cut planes into bands that fit a slot, packed 256-byte aligned, tight pitch = w
@@ -313,8 +323,8 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
             int32_t end = begin;
             while (end < (int32_t)cd.size() && cd[end].cls == c) ++end;
             if (end > begin) {
-                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, c, 0, 4, 2,
-                                                 begin > 0, p->comp));
+                RDCT_CUDA_TRY(launch_fused_batch(s.d_jobs, s.d_chunks + begin, end - begin, p->d_acc, acc8, c, 0, 4,
+                                                 2, begin > 0, p->comp));
             }
             begin = end;
         }
@@ -329,7 +339,7 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
         RDCT_CUDA_TRY(cudaEventRecord(s.out_done, p->d2h));
         s.used = true;
     }
-    return finish_run(p, nimages, sse_per_image);
+    return finish_run(p, nimages, sse_per_image, sse_u8_per_image);
 }
 
 rdct_status rdct_pipeline_destroy(rdct_pipeline *p) {

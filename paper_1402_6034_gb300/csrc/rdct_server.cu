@@ -60,7 +60,7 @@ struct Lane {  // one compute stream and its per-launch resources
     cudaEvent_t done = nullptr;
     JobDesc *d_jobs = nullptr, *h_jobs = nullptr;
     Chunk *d_chunks = nullptr, *h_chunks = nullptr;
-    unsigned long long *d_acc = nullptr, *h_acc = nullptr;
+    unsigned long long *d_acc = nullptr, *h_acc = nullptr;  // per request: 576 * SSE, then the 8-bit error
     int32_t cap_jobs = 0, cap_chunks = 0, cap_acc = 0;
     std::vector<std::shared_ptr<Req>> batch;
     bool busy = false;
@@ -181,19 +181,19 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
         RDCT_CUDA_TRY(cudaStreamWaitEvent(L.s, r.copied, 0));
     }
     std::stable_sort(chunks.begin(), chunks.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
-    if (!grow(L, (int32_t)jobs.size(), (int32_t)chunks.size(), n))
+    if (!grow(L, (int32_t)jobs.size(), (int32_t)chunks.size(), 2 * n))
         return set_error(RDCT_ERR_OOM, "rdct_server: table allocation failed");
     std::memcpy(L.h_jobs, jobs.data(), jobs.size() * sizeof(JobDesc));
     std::memcpy(L.h_chunks, chunks.data(), chunks.size() * sizeof(Chunk));
     RDCT_CUDA_TRY(cudaMemcpyAsync(L.d_jobs, L.h_jobs, jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, L.s));
     RDCT_CUDA_TRY(cudaMemcpyAsync(L.d_chunks, L.h_chunks, chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, L.s));
-    RDCT_CUDA_TRY(cudaMemsetAsync(L.d_acc, 0, n * sizeof(unsigned long long), L.s));
+    RDCT_CUDA_TRY(cudaMemsetAsync(L.d_acc, 0, 2 * n * sizeof(unsigned long long), L.s));
     int32_t begin = 0;
     while (begin < (int32_t)chunks.size()) {
         int32_t end = begin;
         while (end < (int32_t)chunks.size() && chunks[end].cls == chunks[begin].cls) ++end;
-        RDCT_CUDA_TRY(launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, chunks[begin].cls, 0, 4,
-                                         2, begin > 0, L.s));
+        RDCT_CUDA_TRY(launch_fused_batch(L.d_jobs, L.d_chunks + begin, end - begin, L.d_acc, L.d_acc + n,
+                                         chunks[begin].cls, 0, 4, 2, begin > 0, L.s));
         begin = end;
     }
     for (int32_t i = 0; i < n; ++i) {
@@ -205,7 +205,7 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
             RDCT_CUDA_TRY(cudaMemcpy2DAsync(r.q.dst + p * r.q.plane_stride, r.q.pitch, out + p * plane,
                                             r.q.w, r.q.w, r.q.h, cudaMemcpyDeviceToHost, L.s));
     }
-    RDCT_CUDA_TRY(cudaMemcpyAsync(L.h_acc, L.d_acc, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, L.s));
+    RDCT_CUDA_TRY(cudaMemcpyAsync(L.h_acc, L.d_acc, 2 * n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, L.s));
     RDCT_CUDA_TRY(cudaEventRecord(L.done, L.s));
     return RDCT_OK;
 }
@@ -230,12 +230,16 @@ void scheduler(rdct_server *S) {
             if (q == cudaErrorNotReady) continue;
             const rdct_status st = q == cudaSuccess ? RDCT_OK : RDCT_ERR_CUDA;
             const Clock::time_point t = Clock::now();
-            for (int32_t i = 0; i < (int32_t)L.batch.size(); ++i) {
+            const int32_t nb = (int32_t)L.batch.size();
+            for (int32_t i = 0; i < nb; ++i) {
                 Req &r = *L.batch[i];
                 const double n = (double)r.q.w * r.q.h * r.q.planes;
                 r.res.sse = st == RDCT_OK ? (double)L.h_acc[i] / 576.0 : 0.0;
                 r.res.mse = r.res.sse / n;
                 r.res.psnr = r.res.mse == 0.0 ? INFINITY : 10.0 * std::log10(255.0 * 255.0 / r.res.mse);
+                r.res.sse_u8 = st == RDCT_OK ? (double)L.h_acc[nb + i] : 0.0;
+                r.res.mse_u8 = r.res.sse_u8 / n;
+                r.res.psnr_u8 = r.res.mse_u8 == 0.0 ? INFINITY : 10.0 * std::log10(255.0 * 255.0 / r.res.mse_u8);
                 finish(S, r, st, t);
                 rdct_arena_free(S->arena, r.arena_off);
                 cudaEventDestroy(r.copied);
@@ -374,7 +378,7 @@ rdct_status rdct_server_create(const rdct_server_opts *opts, rdct_server **serve
     for (Lane &L : S->lanes) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-        if (e == cudaSuccess && !grow(L, 4 * opts->max_batch, chunk_bound(*opts), opts->max_batch))
+        if (e == cudaSuccess && !grow(L, 4 * opts->max_batch, chunk_bound(*opts), 2 * opts->max_batch))
             e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
@@ -468,6 +472,7 @@ rdct_status rdct_server_stats_get(rdct_server *S, rdct_server_stats *st) {
     st->batches = S->batches;
     st->p50_us = percentile(S->lat_us, 0.50);
     st->p99_us = percentile(S->lat_us, 0.99);
+    st->p999_us = percentile(S->lat_us, 0.999);
     double sum = 0;
     for (double v : S->lat_us) sum += v;
     st->mean_us = S->lat_us.empty() ? 0.0 : sum / S->lat_us.size();

@@ -73,14 +73,18 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("sse", ctypes.c_double), ("mse", ctypes.c_double),
-                ("psnr", ctypes.c_double), ("latency_us", ctypes.c_double)]
+                ("psnr", ctypes.c_double), ("latency_us", ctypes.c_double), ("sse_u8", ctypes.c_double),
+                ("mse_u8", ctypes.c_double), ("psnr_u8", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "status"}
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
                 ("mean_us", ctypes.c_double), ("gpixels_per_s", ctypes.c_double),
-                ("peak_resident_bytes", ctypes.c_int64)]
+                ("peak_resident_bytes", ctypes.c_int64), ("p999_us", ctypes.c_double)]
 
 
 _lib = None
@@ -98,7 +102,7 @@ _SIGS = {
     "rdct_compress": [_vp, _i64, _i32, _vp, _vp],
     "rdct_inverse": [_vp, _i64, _i64, _i32, ctypes.c_int, ctypes.POINTER(Out), _vp],
     "rdct_mse_psnr": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp, _vp],
-    "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp],
+    "rdct_fused": [ctypes.POINTER(Plane), _i32, ctypes.c_int, ctypes.POINTER(Out), _vp, _vp, _vp],
     "rdct_uqi": [ctypes.POINTER(Plane), ctypes.POINTER(Out), _vp, _vp],
     "rdct_variant_matrices": [ctypes.c_int, _vp, _vp],
     "rdct_pipeline_set_mode": [_vp, _i32],
@@ -107,14 +111,14 @@ _SIGS = {
     "rdct_sweep": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_sweep_noalloc": [ctypes.POINTER(Plane), _i32, ctypes.c_int, _vp, _vp],
     "rdct_batch_plan_create": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), ctypes.POINTER(_vp)],
-    "rdct_batch_run": [_vp, _vp, _vp],
-    "rdct_batch_run_per_plane": [_vp, _vp, _vp],
+    "rdct_batch_run": [_vp, _vp, _vp, _vp],
+    "rdct_batch_run_per_plane": [_vp, _vp, _vp, _vp],
     "rdct_batch_plan_get_tune": [_vp, ctypes.POINTER(Tune)],
     "rdct_batch_plan_kernels": [_vp, ctypes.POINTER(_i32)],
     "rdct_batch_plan_destroy": [_vp],
     "rdct_autotune": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), _vp],
     "rdct_pipeline_create": [_i64, _i32, ctypes.POINTER(_vp)],
-    "rdct_pipeline_run": [_vp, ctypes.POINTER(HostJob), _i32, _i32, _vp],
+    "rdct_pipeline_run": [_vp, ctypes.POINTER(HostJob), _i32, _i32, _vp, _vp],
     "rdct_pipeline_destroy": [_vp],
     "rdct_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(_vp)],
     "rdct_server_submit": [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
@@ -312,18 +316,23 @@ def fused_variant(img: torch.Tensor, r: int, variant: int, want_u8: bool = True,
 
 
 def fused(img: torch.Tensor, r: int, kind: int = KIND_RDCT, want_u8: bool = True, want_f32: bool = False,
-          out_u8: torch.Tensor | None = None, sse: torch.Tensor | None = None, stream=None):
-    """Forward + keep r + inverse + SSE in one kernel; returns (u8 or None, f32 or None, sse [1] float64)."""
+          out_u8: torch.Tensor | None = None, sse: torch.Tensor | None = None, sse_u8: torch.Tensor | None = None,
+          stream=None):
+    """Forward + keep r + inverse + SSE in one kernel; returns (u8 or None, f32 or None, sse [1] float64).
+    sse_u8 (a float64 CUDA tensor of one element, or None) receives the squared error of the 8-bit
+    reconstruction."""
     p = plane_of(img)
     dev = img.device
     u8 = out_u8 if out_u8 is not None else (torch.empty((p.h, p.w), dtype=torch.uint8, device=dev) if want_u8 else None)
     f32 = torch.empty((p.h, p.w), dtype=torch.float32, device=dev) if want_f32 else None
     if sse is None:
         sse = torch.empty(1, dtype=torch.float64, device=dev)
+    if sse_u8 is not None:
+        _require_cuda(sse_u8, "sse_u8", torch.float64)
     out = Out(u8.data_ptr() if u8 is not None else None, f32.data_ptr() if f32 is not None else None,
               u8.stride(0) if u8 is not None else 0, p.w)
-    _check(load().rdct_fused(ctypes.byref(p), r, kind, ctypes.byref(out), sse.data_ptr(), _stream(stream)),
-           "rdct_fused")
+    _check(load().rdct_fused(ctypes.byref(p), r, kind, ctypes.byref(out), sse.data_ptr(),
+                             sse_u8.data_ptr() if sse_u8 is not None else None, _stream(stream)), "rdct_fused")
     return u8, f32, sse
 
 
@@ -356,11 +365,6 @@ def plane_array(planes) -> ctypes.Array:
     if isinstance(planes, torch.Tensor) and planes.dim() == 3:
         planes = list(planes.unbind(0))
     return (Plane * len(planes))(*[plane_of(t) for t in planes])
-
-
-def psnr_of_mse(mse):
-    """PSNR = 10 log10(255^2 / MSE) for a tensor of MSE values (inf where MSE = 0)."""
-    return 10.0 * torch.log10((255.0 ** 2) / mse)
 
 
 # ----------------------------------------------------------------- batches
@@ -409,11 +413,15 @@ class BatchPlan:
         _check(load().rdct_batch_plan_kernels(self._h, ctypes.byref(k)), "rdct_batch_plan_kernels")
         return int(k.value)
 
-    def run(self, sse: torch.Tensor, stream=None):
-        _check(load().rdct_batch_run(self._h, sse.data_ptr(), _stream(stream)), "rdct_batch_run")
+    def run(self, sse: torch.Tensor, stream=None, sse_u8: torch.Tensor | None = None):
+        """sse (and sse_u8 if given): float64 CUDA tensors of nimages elements."""
+        _check(load().rdct_batch_run(self._h, sse.data_ptr(), sse_u8.data_ptr() if sse_u8 is not None else None,
+                                     _stream(stream)), "rdct_batch_run")
 
-    def run_per_plane(self, sse: torch.Tensor, stream=None):
-        _check(load().rdct_batch_run_per_plane(self._h, sse.data_ptr(), _stream(stream)), "rdct_batch_run_per_plane")
+    def run_per_plane(self, sse: torch.Tensor, stream=None, sse_u8: torch.Tensor | None = None):
+        _check(load().rdct_batch_run_per_plane(self._h, sse.data_ptr(),
+                                               sse_u8.data_ptr() if sse_u8 is not None else None, _stream(stream)),
+               "rdct_batch_run_per_plane")
 
     def close(self):
         if self._h:
@@ -453,8 +461,9 @@ class Pipeline:
         self._h = h
         _check(load().rdct_pipeline_set_mode(h, mode), "rdct_pipeline_set_mode")
 
-    def run(self, jobs: list[tuple], nimages: int):
-        """jobs: (src, dst or None, r, image) with src/dst 2-D uint8 host arrays (numpy or CPU tensors)."""
+    def run(self, jobs: list[tuple], nimages: int, want_u8_error: bool = False):
+        """jobs: (src, dst or None, r, image) with src/dst 2-D uint8 host arrays (numpy or CPU tensors).
+        Returns the per-image SSE list, or (SSE list, 8-bit SSE list) with want_u8_error."""
         arr = (HostJob * len(jobs))()
         keep = []
         for i, (src, dst, r, image) in enumerate(jobs):
@@ -463,7 +472,10 @@ class Pipeline:
             arr[i] = HostJob(sp, dp, pitch, w, h, r, image)
             keep.append((src, dst))
         sse = (ctypes.c_double * max(nimages, 1))()
-        _check(load().rdct_pipeline_run(self._h, arr, len(jobs), nimages, sse), "rdct_pipeline_run")
+        sse8 = (ctypes.c_double * max(nimages, 1))() if want_u8_error else None
+        _check(load().rdct_pipeline_run(self._h, arr, len(jobs), nimages, sse, sse8), "rdct_pipeline_run")
+        if want_u8_error:
+            return list(sse[:nimages]), list(sse8[:nimages])
         return list(sse[:nimages])
 
     def close(self):
@@ -529,7 +541,7 @@ class Server:
         if st != 6:  # keep buffers alive while still pending
             self._keep.pop(ticket, None)
         _check(st, "rdct_server_wait")
-        return {"sse": res.sse, "mse": res.mse, "psnr": res.psnr, "latency_us": res.latency_us}
+        return res.as_dict()
 
     def poll(self, ticket: int):
         res = Result()
@@ -538,7 +550,7 @@ class Server:
             return None
         self._keep.pop(ticket, None)
         _check(st, "rdct_server_poll")
-        return {"sse": res.sse, "mse": res.mse, "psnr": res.psnr, "latency_us": res.latency_us}
+        return res.as_dict()
 
     def cancel(self, ticket: int):
         _check(load().rdct_server_cancel(self._h, ticket), "rdct_server_cancel")

@@ -19,7 +19,7 @@ int main(void) {
     printf("forward %d %s\n", (int)st, strstr(msg, "multiples of 8") ? "detail-ok" : msg);
     /* r = 0 is out of range: RDCT_ERR_ARG */
     rdct_plane ok = {(const uint8_t *)16, 16, 16, 8};
-    st = rdct_fused(&ok, 0, RDCT_KIND_RDCT, NULL, (double *)16, NULL);
+    st = rdct_fused(&ok, 0, RDCT_KIND_RDCT, NULL, (double *)16, NULL, NULL);
     printf("fused %d\n", (int)st);
     /* a batch job with a bad plane names the job */
     rdct_job jobs[1];

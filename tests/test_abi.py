@@ -54,10 +54,13 @@ def test_validation_happens_before_any_launch():
     assert lib.rdct_forward(ctypes.byref(bad), ctypes.c_void_p(16), None) == 2
     assert "multiples of 8" in _last_error()
     ok = rdct.Plane(ctypes.c_void_p(16), 16, 16, 8)
-    assert lib.rdct_fused(ctypes.byref(ok), 0, 0, None, ctypes.c_void_p(16), None) == 1  # r = 0
-    assert lib.rdct_fused(ctypes.byref(ok), 65, 0, None, ctypes.c_void_p(16), None) == 1  # r = 65
-    assert lib.rdct_fused(ctypes.byref(ok), 10, 7, None, ctypes.c_void_p(16), None) == 1  # bad kind
-    assert lib.rdct_fused(None, 10, 0, None, ctypes.c_void_p(16), None) == 1
+    assert lib.rdct_fused(ctypes.byref(ok), 0, 0, None, ctypes.c_void_p(16), None, None) == 1  # r = 0
+    assert lib.rdct_fused(ctypes.byref(ok), 65, 0, None, ctypes.c_void_p(16), None, None) == 1  # r = 65
+    assert lib.rdct_fused(ctypes.byref(ok), 10, 7, None, ctypes.c_void_p(16), None, None) == 1  # bad kind
+    assert lib.rdct_fused(None, 10, 0, None, ctypes.c_void_p(16), None, None) == 1
+    # the 8-bit error slot must be aligned and distinct from the SSE slot
+    assert lib.rdct_fused(ctypes.byref(ok), 10, 0, None, ctypes.c_void_p(16), ctypes.c_void_p(20), None) == 1
+    assert lib.rdct_fused(ctypes.byref(ok), 10, 0, None, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
     short = rdct.Plane(ctypes.c_void_p(16), 8, 16, 8)  # pitch < width
     assert lib.rdct_forward(ctypes.byref(short), ctypes.c_void_p(16), None) == 2
     assert lib.rdct_compress(None, 4, 10, ctypes.c_void_p(16), None) == 1
@@ -98,6 +101,12 @@ def test_batch_job_errors_name_the_job_and_keep_the_detail():
 def test_binding_has_sync():
     assert callable(rdct.sync)
     assert "rdct_sync" in rdct._SIGS
+
+
+def test_batch_run_rejects_bad_error_slots():
+    lib = rdct.load()
+    assert lib.rdct_batch_run(None, ctypes.c_void_p(16), None, None) == 1
+    assert lib.rdct_batch_run_per_plane(None, ctypes.c_void_p(16), None, None) == 1
 
 
 def test_batch_plan_kernels_rejects_null():

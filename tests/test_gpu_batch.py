@@ -129,6 +129,74 @@ def test_batch_mixed_staging(dev):
             assert torch.equal(a, j.dst)
 
 
+def _tune(bpt):
+    return {"warps_per_cta": 4 if bpt == 2 else 8, "ctas_per_sm": 0, "items_per_chunk": 16, "blocks_per_thread": bpt}
+
+
+def test_dropped_coefficient_form_matches_the_scalar_kernel(dev):
+    """From r = 33 the two-block kernel rebuilds each block as 576 A - C0^T (W o Y_dropped) C0 from the
+    coefficients it drops; the scalar kernel still inverts the kept ones.  The two must agree bit for bit
+    (reconstruction, exact SSE and the 8-bit error) at every r from 32 to 64, for planes that take TMA
+    staging (16-byte aligned, full 32-column segments) and planes that take the per-thread copies (an
+    8-byte pitch), each with an odd number of block rows."""
+    rng = np.random.Generator(np.random.PCG64(33))
+    pool = synth.crop_pool(pool_side=512, n=2, seed=33)
+    jobs, host = [], []
+    for k, r in enumerate(range(32, 65)):
+        for (h, w, sp) in ((72, 256, 256), (40, 200, 208)):
+            img = synth.crop_plane(pool, h, w, rng)
+            sbuf = torch.zeros(h * sp, dtype=torch.uint8, device=dev)
+            src = torch.as_strided(sbuf, (h, w), (sp, 1))
+            src.copy_(to_dev(img, dev))
+            dst = torch.zeros((h, w), dtype=torch.uint8, device=dev)
+            jobs.append(rdct.BatchJob(src, dst, r, len(host)))
+            host.append((img, r, len(host)))
+    n = len(host)
+    out = {}
+    for bpt in (2, 1):
+        plan = rdct.BatchPlan(jobs, n, tune=_tune(bpt))
+        sse = torch.empty(n, dtype=torch.float64, device=dev)
+        sse8 = torch.empty(n, dtype=torch.float64, device=dev)
+        plan.run(sse, sse_u8=sse8)
+        rdct.sync()
+        out[bpt] = (sse.clone(), sse8.clone(), [j.dst.clone() for j in jobs])
+        plan.close()
+    assert torch.equal(out[2][0], out[1][0])
+    assert torch.equal(out[2][1], out[1][1])
+    for a, b in zip(out[2][2], out[1][2]):
+        assert torch.equal(a, b)
+    _check_against_oracle(list(range(n)), jobs, host, out[2][0].cpu().numpy())
+    for (img, r, i), d in zip(host, out[2][2]):
+        assert out[2][1][i].item() == orc.sse(img, d.cpu().numpy())
+
+
+def test_batch_u8_error_every_staging(dev):
+    """The 8-bit error per image from the graph launch equals that of the returned planes (summed over
+    an image's planes), for both stagings and both forms, and asking for it changes nothing else."""
+    specs, jobs, host = _batch(dev, n_images=14, seed=17, rs=(4, 16, 21, 32, 40, 57, 64), lo=64, hi=520)
+    n = len(specs)
+    plan = rdct.BatchPlan(jobs, n)
+    sse = torch.empty(n, dtype=torch.float64, device=dev)
+    sse8 = torch.empty(n, dtype=torch.float64, device=dev)
+    plan.run(sse, sse_u8=sse8)
+    rdct.sync()
+    outs = [j.dst.clone() for j in jobs]
+    ref8 = np.zeros(n)
+    for (img, r, i), d in zip(host, outs):
+        ref8[i] += orc.sse(img, d.cpu().numpy())
+    np.testing.assert_array_equal(sse8.cpu().numpy(), ref8)
+    sse_plain = torch.empty(n, dtype=torch.float64, device=dev)
+    plan.run(sse_plain)  # a second graph without the 8-bit error
+    sse_pp = torch.empty(n, dtype=torch.float64, device=dev)
+    sse8_pp = torch.empty(n, dtype=torch.float64, device=dev)
+    plan.run_per_plane(sse_pp, sse_u8=sse8_pp)
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(sse, sse_plain) and torch.equal(sse, sse_pp) and torch.equal(sse8, sse8_pp)
+    for a, j in zip(outs, jobs):
+        assert torch.equal(a, j.dst)
+
+
 def test_batch_equals_per_plane(dev):
     specs, jobs, host = _batch(dev, n_images=20, seed=9)
     plan = rdct.BatchPlan(jobs, len(specs), tune={"warps_per_cta": 4, "ctas_per_sm": 2, "items_per_chunk": 3})

@@ -121,6 +121,45 @@ def test_fused_every_r(dev, r):
     assert float(sse.item()) == pytest.approx(so, rel=1e-9, abs=1e-9)
 
 
+@pytest.mark.parametrize("r", list(range(1, 65)))
+def test_fused_two_block_kernel_every_r_with_u8_error(dev, r):
+    """The two-block kernel (uint8 output, no FP32 output) at every r: the reconstruction from the
+    kept coefficients up to r = 32 and from the dropped ones above, and the squared error of the
+    8-bit reconstruction.  9 block rows, so the last row pair has one block."""
+    img = _img(72, 136, 2000 + r, "noise" if r % 2 else "1f")
+    xo, uo, so, s8o = orc.fused(img, r)
+    t = to_dev(img, dev)
+    sse8 = torch.empty(1, dtype=torch.float64, device=dev)
+    u8, _, sse = rdct.fused(t, r, sse_u8=sse8)
+    g = u8.cpu().numpy()
+    assert_u8_close(g, uo, xo, tie_window=1e-6)
+    assert float(sse.item()) == pytest.approx(so, rel=1e-9, abs=1e-9)
+    # exactly the error of the 8-bit image returned, and the oracle's wherever no pixel sits at a half
+    assert float(sse8.item()) == orc.sse(img, g)
+    if np.array_equal(g, uo):
+        assert float(sse8.item()) == s8o
+    # error only: nothing stored, the same two errors
+    sse8b = torch.empty(1, dtype=torch.float64, device=dev)
+    _, _, sseb = rdct.fused(t, r, want_u8=False, sse_u8=sse8b)
+    assert float(sseb.item()) == float(sse.item()) and float(sse8b.item()) == float(sse8.item())
+    # without the 8-bit error the reconstruction and the error are the same
+    u8c, _, ssec = rdct.fused(t, r)
+    assert torch.equal(u8c, u8) and float(ssec.item()) == float(sse.item())
+
+
+@pytest.mark.parametrize("kind", [rdct.KIND_RDCT, rdct.KIND_DCT])
+@pytest.mark.parametrize("r", [1, 10, 33, 64])
+def test_u8_error_with_fp32_output(dev, kind, r):
+    """The single-block kernels (FP32 output, exact DCT) report the 8-bit error too."""
+    img = _img(40, 264, 300 + r)
+    sse8 = torch.empty(1, dtype=torch.float64, device=dev)
+    u8, f32, _ = rdct.fused(to_dev(img, dev), r, kind, want_u8=True, want_f32=True, sse_u8=sse8)
+    assert float(sse8.item()) == orc.sse(img, u8.cpu().numpy())
+    sse8b = torch.empty(1, dtype=torch.float64, device=dev)
+    rdct.fused(to_dev(img, dev), r, kind, want_u8=False, want_f32=True, sse_u8=sse8b)
+    assert float(sse8b.item()) == float(sse8.item())
+
+
 @pytest.mark.parametrize("h,w", SHAPES + [(2048, 2048)])
 @pytest.mark.parametrize("r", [1, 10, 16, 64])
 def test_fused_shapes(dev, h, w, r):

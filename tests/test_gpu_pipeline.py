@@ -82,6 +82,20 @@ def test_pipeline_against_oracle(dev):
         assert sse[img] == pytest.approx(tot[img], rel=1e-9, abs=1e-9)
 
 
+@pytest.mark.parametrize("mode", [rdct.Pipeline.STAGED, rdct.Pipeline.DIRECT])
+def test_pipeline_u8_error(dev, mode):
+    """Both modes return each image's 8-bit error: that of the planes they wrote back."""
+    jobs = _planes(4, True)
+    p = rdct.Pipeline(device_budget_bytes=8 << 20, depth=3, mode=mode)
+    sse, sse8 = p.run(jobs, 4, want_u8_error=True)
+    p.close()
+    ref8 = np.zeros(4)
+    for src, dst, r, img in jobs:
+        ref8[img] += orc.sse(np.ascontiguousarray(src.numpy()), np.ascontiguousarray(dst.numpy()))
+    np.testing.assert_array_equal(np.array(sse8), ref8)
+    np.testing.assert_allclose(sse, _device_reference(jobs, dev)[1], rtol=1e-12, atol=1e-9)
+
+
 def test_pipeline_sse_only_and_direct_refuses_pageable(dev):
     jobs = [(src, None, r, img) for src, _, r, img in _planes(3, True)]
     ref = _device_reference(jobs, dev)[1]

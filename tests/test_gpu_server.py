@@ -65,8 +65,11 @@ def test_results_match_oracle(dev):
         assert rr["sse"] == pytest.approx(sse, rel=1e-9, abs=1e-9)
         for p, (xo, uo) in enumerate(per_plane):
             assert_u8_close(out[p].numpy(), uo, xo, tie_window=1e-6)
+        # the 8-bit error is that of the image returned
+        assert rr["sse_u8"] == sum(orc.sse(src[p].numpy(), out[p].numpy()) for p in range(src.shape[0]))
+        assert rr["mse_u8"] == pytest.approx(rr["sse_u8"] / src.numel(), rel=1e-15)
     st = srv.stats()
-    assert st["completed"] == 12 and st["p99_us"] >= st["p50_us"] > 0
+    assert st["completed"] == 12 and st["p999_us"] >= st["p99_us"] >= st["p50_us"] > 0
     srv.close()
 
 
@@ -82,7 +85,7 @@ def test_alone_equals_mixed(dev):
     assert srv.stats()["batches"] < len(reqs)  # they really were batched
     srv.close()
     for (o_a, r_a), o_m, r_m in zip(alone, outs, res):
-        assert r_a[0]["sse"] == r_m["sse"]
+        assert r_a[0]["sse"] == r_m["sse"] and r_a[0]["sse_u8"] == r_m["sse_u8"]
         assert torch.equal(o_a[0], o_m)
 
 
