@@ -104,14 +104,14 @@ __host__ __device__ constexpr unsigned c0_row_word(int k, int half) {
 // path are integers below 2^24 in magnitude, so FP32 is exact here.
 
 template <bool A, bool B, typename V>
-__device__ __forceinline__ V padd(V a, V b) {
+__host__ __device__ __forceinline__ V padd(V a, V b) {
     if constexpr (A && B) return a + b;
     else if constexpr (A) return a;
     else if constexpr (B) return b;
     else return V{};
 }
 template <bool A, bool B, typename V>
-__device__ __forceinline__ V psub(V a, V b) {
+__host__ __device__ __forceinline__ V psub(V a, V b) {
     if constexpr (A && B) return a - b;
     else if constexpr (A) return a;
     else if constexpr (B) return -b;
@@ -122,8 +122,9 @@ __device__ __forceinline__ V psub(V a, V b) {
 // at compile time to be zero (bit k of M set = X[k] may be non-zero).  V is
 // float or a packed pair of floats; on the RDCT path every value is an
 // integer (in some fixed unit) below 2^24 in magnitude, so it is exact.
+// (Host-callable so that its operation count can be checked.)
 template <unsigned M, typename V>
-__device__ __forceinline__ void c0t_inverse(const V X[8], V x[8]) {
+__host__ __device__ __forceinline__ void c0t_inverse(const V X[8], V x[8]) {
     constexpr bool p0 = M & 1u, p1 = (M >> 1) & 1u, p2 = (M >> 2) & 1u, p3 = (M >> 3) & 1u;
     constexpr bool p4 = (M >> 4) & 1u, p5 = (M >> 5) & 1u, p6 = (M >> 6) & 1u, p7 = (M >> 7) & 1u;
     // even half: columns n = 0..3 of rows 0, 2, 4, 6

@@ -23,7 +23,7 @@
 //   * error: 576 SSE = 576 sum x^2 - sum_kept W Y^2 (Parseval, the transform
 //     is orthogonal), with sum x^2 from dp4a and the kept energies summed
 //     per weight group in 32 bits: exact;
-//   * for r > 32 the same integers come from the coefficients that are
+//   * from r = 36 the same integers come from the coefficients that are
 //     dropped instead (576 Xhat = 576 A - C0^T (W o Y_dropped) C0 and
 //     576 SSE = sum_dropped W Y^2), so the work shrinks as r approaches 64,
 //     where the reconstruction is the block itself;
@@ -125,8 +125,14 @@ __host__ __device__ constexpr unsigned drop_row_mask(int R) {
 //   576 Xhat = 576 A - C0^T (W o Y_dropped) C0,
 //   576 SSE  = sum over the dropped positions of W Y^2   (Parseval),
 // the same integers as the kept form, in work that shrinks with 64 - r.
-__host__ __device__ constexpr bool drop_form(int R) { return R > 32; }
+// Measured on a 600-frame 4K clip (fraction of HBM, kept / dropped form):
+// r = 33 0.713 / 0.672, r = 35 0.712 / 0.701, r = 36 0.697 / 0.729,
+// r = 40 0.685 / 0.798, r = 44 0.650 / 0.815; so the dropped form from r = 36.
+__host__ __device__ constexpr bool drop_form(int R) { return R > 35; }
 
+// Y = C0 A C0^T of one block: every output of the row pass is a pair of byte
+// dot products of the packed pixels with a row of C0 as signed bytes (dp4a),
+// the column pass the 22-addition butterfly in int32.
 __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][8]) {
     int R[8][8];
 #pragma unroll
@@ -142,6 +148,67 @@ __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][
         c0_forward(c, o);
 #pragma unroll
         for (int i = 0; i < 8; ++i) Y[i][j] = o[i];
+    }
+}
+
+// The forward transform of both blocks of a column pair at once, on packed
+// pairs of 16-bit lanes (block a low, block b high): an addition or
+// subtraction of two 32-bit words is exact in each lane as long as every true
+// lane value stays within [-32768, 32767] (a carry or borrow out of the low
+// lane is absorbed when the lanes are read back: lo = the sign-extended low
+// half, hi = (word + 2^15) >> 16).  Every value on the path is at most
+// 8 * 2040 = 16320 in magnitude, so the 22-addition butterflies of the row and
+// the column pass serve both blocks with one integer addition each, on the
+// integer ALU, instead of byte dot products on the multiply pipe.  The
+// compiler drops every output (and lane read) that the zone in use never needs.
+__device__ __forceinline__ void forward_pair16(const uint2 (&wa)[8], const uint2 (&wb)[8], int (&Ya)[8][8],
+                                               int (&Yb)[8][8]) {
+    unsigned R[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        unsigned x[8];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            // byte n of each block's word into the low byte of its lane
+            const unsigned sel = (unsigned)n * 0x11u + (unsigned)(4 + n) * 0x1100u;
+            x[n] = __byte_perm(wa[i].x, wb[i].x, sel) & 0x00FF00FFu;
+            x[n + 4] = __byte_perm(wa[i].y, wb[i].y, sel) & 0x00FF00FFu;
+        }
+        c0_forward(x, R[i]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        unsigned c[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = R[i][j];
+        c0_forward(c, o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            Ya[i][j] = (int)(int16_t)(o[i] & 0xFFFFu);
+            Yb[i][j] = ((int)o[i] + 0x8000) >> 16;
+        }
+    }
+}
+
+// Which form of the forward transform a kernel for exactly R kept
+// coefficients uses: the packed 16-bit lanes move the work from the multiply
+// pipe (dp4a) to the integer ALU, which pays where the multiply pipe is the
+// busier one.  Measured on a 600-frame 4K clip, packed against dp4a: +1 to
+// +2% at r = 16..23, +1 to +3.5% at r = 29..34, +1 to +2% at r = 55..58;
+// within 0.5% at r = 6..12 and 24; 3 to 7% slower at r = 36..53 (there the
+// reconstruction from the dropped coefficients already loads the ALU).
+__host__ __device__ constexpr bool packed_forward(int R) {
+    return (R >= 16 && R <= 24) || (R >= 28 && R <= 34) || (R >= 55 && R <= 58);
+}
+
+template <int R>
+__device__ __forceinline__ void forward_pair(const uint2 (&wa)[8], const uint2 (&wb)[8], int (&Ya)[8][8],
+                                             int (&Yb)[8][8]) {
+    if constexpr (packed_forward(R)) {
+        forward_pair16(wa, wb, Ya, Yb);
+    } else {
+        forward_c0_int(wa, Ya);
+        forward_c0_int(wb, Yb);
     }
 }
 
@@ -296,8 +363,7 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
         return 0ull;
     } else if constexpr (drop_form(R)) {
         int Ya[8][8], Yb[8][8];
-        forward_c0_int(wa, Ya);
-        forward_c0_int(wb, Yb);
+        forward_pair<R>(wa, wb, Ya, Yb);
         // Z = -W Y on the dropped coefficients, so that the inverse yields -D
         f2 Z[8][8];
         const unsigned long long dropped = zone_to_z<R, false, -1>(Ya, Yb, Z);
@@ -326,8 +392,7 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
     } else {
         sumsq = pair_sumsq(wa, wb);
         int Ya[8][8], Yb[8][8];
-        forward_c0_int(wa, Ya);
-        forward_c0_int(wb, Yb);
+        forward_pair<R>(wa, wb, Ya, Yb);
         f2 Z[8][8];
         const unsigned long long kept = zone_to_z<R, true, 1>(Ya, Yb, Z);
         if (rec) {
@@ -348,15 +413,17 @@ __device__ __forceinline__ unsigned long long fused2_pair(const uint2 (&wa)[8], 
 // ------------------------------------------------------------------ kernel
 
 // Launch shape per r: 128 registers (four CTAs of 128 threads per SM) up to
-// r = 26, 168 (three CTAs) above, and never more than kFused2MaxCtas CTAs per
-// SM (see launch_staged).  Measured on a 600-frame 4K clip: four CTAs are 1%
-// faster at r = 25; three are 2% faster at r = 28 and 2-4% at r = 32-36 (no
-// spills), and two CTAs with 255 registers were 4-8% slower from r = 45 up.
-// Shared memory beyond four rings squeezes the L1 the copies go through.
-template <int R>
+// r = 34, 168 (three CTAs) above, and never more than kFused2MaxCtas CTAs per
+// SM (see launch_staged).  Measured on a 600-frame 4K clip with the forward
+// forms of packed_forward: four CTAs are 1.6 to 3.7% faster than three at
+// r = 27..34, within 0.2% up to r = 26, and 1 to 5.5% slower at r = 35..40
+// (two CTAs with 255 registers were 4-8% slower from r = 45 up).  Shared
+// memory beyond four rings squeezes the L1 the copies go through.
+template <int R, bool E8 = false>
 struct Fused2Shape {
     static constexpr int threads = 128;
-    static constexpr int min_blocks = R <= 26 ? 4 : 3;
+    // the 8-bit error's extra accumulators spill at 128 registers from r = 24
+    static constexpr int min_blocks = R <= (E8 ? 23 : 34) ? 4 : 3;
 };
 constexpr int kStages = 2;   // cp.async ring depth per thread (double buffer)
 constexpr int kVRows = kFusedVRows;  // vertically adjacent blocks per thread per strip
@@ -744,11 +811,11 @@ constexpr bool tma_store_pays(int R) { return R > 16; }
 // TMA-staged batch launch for exactly r = R (instantiated with the others).
 template <int R>
 cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap, cudaStream_t s) {
-    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
+    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks, MB8 = Fused2Shape<R, true>::min_blocks;
     constexpr bool TS = tma_store_pays(R);
     constexpr int smem = (T / 32) * kStages * kTmaBoxBytes;
     if (a.acc8 != nullptr)
-        return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS, true>, a.nchunks, ctas_per_sm, T / 32,
+        return launch_staged(fused2_tma_kernel<R - 1, T, MB8, TS, true>, a.nchunks, ctas_per_sm, T / 32,
                              kFused2MaxCtas, smem, overlap, s, a);
     return launch_staged(fused2_tma_kernel<R - 1, T, MB, TS, false>, a.nchunks, ctas_per_sm, T / 32, kFused2MaxCtas,
                          smem, overlap, s, a);
@@ -760,14 +827,14 @@ cudaError_t launch_fused2_tma_r(const TmaArgs &a, int ctas_per_sm, bool overlap,
 // stream (batch launches after the first of a batch).
 template <int R>
 cudaError_t launch_fused2_r(const Fused2Args &a, bool single, int ctas_per_sm, bool overlap, cudaStream_t s) {
-    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks;
+    constexpr int T = Fused2Shape<R>::threads, MB = Fused2Shape<R>::min_blocks, MB8 = Fused2Shape<R, true>::min_blocks;
     const bool e8 = a.acc8 != nullptr;
     if (single)
-        return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB, true>, a.nchunks, ctas_per_sm, T / 32,
+        return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB8, true>, a.nchunks, ctas_per_sm, T / 32,
                                   kFused2MaxCtas, kFused2Smem, false, s, a)
                   : launch_staged(fused2_kernel<R - 1, R - 1, true, T, MB, false>, a.nchunks, ctas_per_sm, T / 32,
                                   kFused2MaxCtas, kFused2Smem, false, s, a);
-    return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB, true>, a.nchunks, ctas_per_sm, T / 32,
+    return e8 ? launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB8, true>, a.nchunks, ctas_per_sm, T / 32,
                               kFused2MaxCtas, kFused2Smem, overlap, s, a)
               : launch_staged(fused2_kernel<R - 1, R - 1, false, T, MB, false>, a.nchunks, ctas_per_sm, T / 32,
                               kFused2MaxCtas, kFused2Smem, overlap, s, a);

@@ -36,51 +36,89 @@ __global__ void sse576_to_double_kernel(void *slots, void *slots8, int32_t n) {
 
 // ------------------------------------------------------- forward kernels
 
-__global__ void __launch_bounds__(256) forward_kernel(const JobDesc job, int32_t *__restrict__ Y) {
-    const int64_t nblocks = (int64_t)job.nbw * job.nbh;
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const int by = (int)(b / job.nbw), bx = (int)(b - (int64_t)by * job.nbw);
-        uint32_t w[16];
-        load_block(job.src + (int64_t)by * 8 * job.src_pitch + (int64_t)bx * 8, job.src_pitch, job.align, w);
-        int Yb[8][8];
-        forward_c0(w, Yb);
-        int4 *out = reinterpret_cast<int4 *>(Y + b * 64);
+// One warp per 32 consecutive blocks (block index b = by * nbw + bx, so their
+// coefficients are one contiguous 8 KB run of Y): each lane transforms its
+// block and writes its 64 values to the warp's shared-memory stage (16-byte
+// words swizzled so that neither the writes nor the reads conflict on banks),
+// and the warp then stores the run with every store instruction covering 512
+// contiguous bytes.
+constexpr int kFwdWarps = 4;
+
+// Lane's block row i (8 values of 4 bytes) into the stage.
+__device__ __forceinline__ void stage_row(int4 *st, int lane, int i, int4 lo, int4 hi) {
+    st[lane * 16 + ((2 * i) ^ (lane & 7))] = lo;
+    st[lane * 16 + ((2 * i + 1) ^ (lane & 7))] = hi;
+}
+// The warp's staged run (nvalid blocks of 256 bytes) to out.
+__device__ __forceinline__ void store_run(const int4 *st, int4 *out, int64_t nvalid, int lane) {
+    __syncwarp();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            __stcs(out + 2 * i, make_int4(Yb[i][0], Yb[i][1], Yb[i][2], Yb[i][3]));
-            __stcs(out + 2 * i + 1, make_int4(Yb[i][4], Yb[i][5], Yb[i][6], Yb[i][7]));
-        }
+    for (int k = 0; k < 16; ++k) {
+        const int j = k * 32 + lane;  // 16-byte word j of the run: block j / 16, word j % 16
+        const int jb = j >> 4, jw = j & 15;
+        if (jb < nvalid) __stcs(out + j, st[jb * 16 + (jw ^ (jb & 7))]);
     }
+    __syncwarp();
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(256) forward_f32_kernel(const JobDesc job, float *__restrict__ Y,
-                                                          const DctConsts C, const ScaleConsts S) {
+__global__ void __launch_bounds__(kFwdWarps * 32) forward_kernel(const JobDesc job, int32_t *__restrict__ Y) {
+    __shared__ int4 stage[kFwdWarps][32 * 16];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int4 *st = stage[wid];
     const int64_t nblocks = (int64_t)job.nbw * job.nbh;
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const int by = (int)(b / job.nbw), bx = (int)(b - (int64_t)by * job.nbw);
-        uint32_t w[16];
-        load_block(job.src + (int64_t)by * 8 * job.src_pitch + (int64_t)bx * 8, job.src_pitch, job.align, w);
-        float Yf[8][8];
-        if constexpr (KIND == RDCT_KIND_RDCT) {
+    const int64_t step = (int64_t)gridDim.x * kFwdWarps * 32;
+    for (int64_t b0 = ((int64_t)blockIdx.x * kFwdWarps + wid) * 32; b0 < nblocks; b0 += step) {
+        const int64_t b = b0 + lane;
+        if (b < nblocks) {
+            const int64_t by = b / job.nbw, bx = b - by * job.nbw;
+            uint32_t w[16];
+            load_block(job.src + by * 8 * job.src_pitch + bx * 8, job.src_pitch, job.align, w);
             int Yb[8][8];
             forward_c0(w, Yb);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) Yf[i][j] = (float)Yb[i][j] * S.dd[i * 8 + j];
-        } else {
-            float A[8][8];
-            forward_dct(w, Yf, A, C);
+                stage_row(st, lane, i, make_int4(Yb[i][0], Yb[i][1], Yb[i][2], Yb[i][3]),
+                          make_int4(Yb[i][4], Yb[i][5], Yb[i][6], Yb[i][7]));
         }
-        float4 *out = reinterpret_cast<float4 *>(Y + b * 64);
+        store_run(st, reinterpret_cast<int4 *>(Y) + b0 * 16, nblocks - b0 < 32 ? nblocks - b0 : 32, lane);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kFwdWarps * 32) forward_f32_kernel(const JobDesc job, float *__restrict__ Y,
+                                                                     const DctConsts C, const ScaleConsts S) {
+    __shared__ int4 stage[kFwdWarps][32 * 16];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int4 *st = stage[wid];
+    const int64_t nblocks = (int64_t)job.nbw * job.nbh;
+    const int64_t step = (int64_t)gridDim.x * kFwdWarps * 32;
+    for (int64_t b0 = ((int64_t)blockIdx.x * kFwdWarps + wid) * 32; b0 < nblocks; b0 += step) {
+        const int64_t b = b0 + lane;
+        if (b < nblocks) {
+            const int64_t by = b / job.nbw, bx = b - by * job.nbw;
+            uint32_t w[16];
+            load_block(job.src + by * 8 * job.src_pitch + bx * 8, job.src_pitch, job.align, w);
+            float Yf[8][8];
+            if constexpr (KIND == RDCT_KIND_RDCT) {
+                int Yb[8][8];
+                forward_c0(w, Yb);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            __stcs(out + 2 * i, make_float4(Yf[i][0], Yf[i][1], Yf[i][2], Yf[i][3]));
-            __stcs(out + 2 * i + 1, make_float4(Yf[i][4], Yf[i][5], Yf[i][6], Yf[i][7]));
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) Yf[i][j] = (float)Yb[i][j] * S.dd[i * 8 + j];
+            } else {
+                float A[8][8];
+                forward_dct(w, Yf, A, C);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                stage_row(st, lane, i,
+                          make_int4(__float_as_int(Yf[i][0]), __float_as_int(Yf[i][1]), __float_as_int(Yf[i][2]),
+                                    __float_as_int(Yf[i][3])),
+                          make_int4(__float_as_int(Yf[i][4]), __float_as_int(Yf[i][5]), __float_as_int(Yf[i][6]),
+                                    __float_as_int(Yf[i][7])));
         }
+        store_run(st, reinterpret_cast<int4 *>(Y) + b0 * 16, nblocks - b0 < 32 ? nblocks - b0 : 32, lane);
     }
 }
 
@@ -109,99 +147,136 @@ __global__ void compress_kernel(const int32_t *__restrict__ Y, int64_t nblocks, 
 }
 
 // Xhat = C0^T (S Yhat S) C0 for kind RDCT, C^T Yhat C for kind DCT; FP32.
-template <int KIND>
+// D: the anti-diagonal class of r (positions beyond it are zero and skipped).
+// One thread per block; the coefficients are read through L1 (a warp's 32
+// blocks are one contiguous run of 32 r floats), rows are stored 8 pixels (or
+// 8 floats) at a time when the output allows it.
+template <int KIND, int D>
 __global__ void __launch_bounds__(256) inverse_kernel(const float *__restrict__ Yc, int64_t nbw, int64_t nbh,
-                                                      int32_t r, uint8_t *u8, int64_t pitch, float *f32,
-                                                      int64_t pitch_f32, const ZigzagTable zz, const ScaleConsts S,
+                                                      int32_t r, uint8_t *u8, int64_t pitch, int u8_align,
+                                                      float *f32, int64_t pitch_f32, const ScaleConsts S,
                                                       const DctConsts C) {
     const int64_t nblocks = nbw * nbh;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblocks;
          b += (int64_t)gridDim.x * blockDim.x) {
         const int64_t by = b / nbw, bx = b - by * nbw;
         float Z[8][8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) Z[i][j] = 0.0f;
         const float *src = Yc + b * r;
         static_for<0, 64>([&](auto qc) {
             constexpr int q = decltype(qc)::value;
-            constexpr int k = zz_rank(q >> 3, q & 7);
-            if (k < r) {
-                const float v = __ldg(src + k);
-                Z[q >> 3][q & 7] = (KIND == RDCT_KIND_RDCT) ? v * S.dd[q] : v;
+            constexpr int i = q >> 3, j = q & 7;
+            if constexpr (i + j <= D) {
+                constexpr int k = zz_rank(i, j);
+                float v = 0.0f;
+                if (i + j < D || k < r) v = __ldg(src + k);
+                Z[i][j] = (KIND == RDCT_KIND_RDCT) ? v * S.dd[q] : v;
+            } else {
+                Z[i][j] = 0.0f;
             }
         });
         float U[8][8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        static_for<0, 8>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            constexpr unsigned m = col_mask(D, j);
             float in[8], out[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) in[i] = Z[i][j];
-            if constexpr (KIND == RDCT_KIND_RDCT) c0t_inverse<0xFFu>(in, out);
-            else dct_inv8<0xFFu>(in, out, C);
+            if constexpr (m == 0u) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) out[i] = 0.0f;
+            } else if constexpr (KIND == RDCT_KIND_RDCT) {
+                c0t_inverse<m>(in, out);
+            } else {
+                dct_inv8<m>(in, out, C);
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i) U[i][j] = out[i];
-        }
+        });
+        constexpr unsigned rm = row_mask(D);
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
             float X[8];
-            if constexpr (KIND == RDCT_KIND_RDCT) c0t_inverse<0xFFu>(U[n], X);
-            else dct_inv8<0xFFu>(U[n], X, C);
+            if constexpr (KIND == RDCT_KIND_RDCT) c0t_inverse<rm>(U[n], X);
+            else dct_inv8<rm>(U[n], X, C);
             const int64_t row = by * 8 + n;
             if (u8) {
-                uint8_t *p = u8 + row * pitch + bx * 8;
+                int q[8];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    const int q = q_of(X[m]);
-                    p[m] = (uint8_t)(q < 0 ? 0 : (q > 255 ? 255 : q));
-                }
+                for (int m = 0; m < 8; ++m) q[m] = q_of(X[m]);
+                store_row_u8(u8 + row * pitch + bx * 8, u8_align, pack4_sat(q[0], q[1], q[2], q[3]),
+                             pack4_sat(q[4], q[5], q[6], q[7]));
             }
-            if (f32) {
-                float *p = f32 + row * pitch_f32 + bx * 8;
-#pragma unroll
-                for (int m = 0; m < 8; ++m) p[m] = X[m];
-            }
+            if (f32) store_row_f32(f32 + row * pitch_f32 + bx * 8, X);
         }
     }
 }
 
 // ------------------------------------------------------------ SSE / PSNR
 
+// Squared error of a reconstruction against a plane.  One warp per row at a
+// time, lanes stepping across it: V pixels per lane and step (16 when both
+// planes start on 16-byte boundaries with 16-byte pitches, 8 when on 8-byte
+// ones, else 1).  For uint8 reconstructions sum (a - b)^2 = sum a^2 + sum b^2
+// - 2 sum a b is formed exactly from byte dot products.
+template <int V>
+__device__ __forceinline__ void load_px(const uint8_t *p, uint32_t (&w)[V / 4 > 0 ? V / 4 : 1]) {
+    if constexpr (V == 16) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(p));
+        w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    } else if constexpr (V == 8) {
+        const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p));
+        w[0] = v.x, w[1] = v.y;
+    } else {
+        w[0] = p[0];
+    }
+}
+
+template <int V, bool U8>
 __global__ void __launch_bounds__(256) sse_kernel(const JobDesc ref, const uint8_t *__restrict__ rec_u8,
                                                   int64_t rec_pitch, const float *__restrict__ rec_f32,
                                                   int64_t rec_pitch_f32, unsigned long long *acc_u64,
                                                   double *acc_f64) {
-    const int64_t groups_per_row = ref.nbw;  // 8-pixel groups
-    const int64_t total = groups_per_row * (int64_t)ref.nbh * 8;
+    constexpr int NW = V / 4 > 0 ? V / 4 : 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t h = (int64_t)ref.nbh * 8, w = (int64_t)ref.nbw * 8;
     unsigned long long su = 0;
     double sf = 0.0;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t y = g / groups_per_row, x = (g - y * groups_per_row) * 8;
-        const uint8_t *a = ref.src + y * ref.src_pitch + x;
-        if (rec_u8) {
-            const uint8_t *b = rec_u8 + y * rec_pitch + x;
-            unsigned s = 0;
+    for (int64_t y = warp; y < h; y += nwarps) {
+        const uint8_t *a = ref.src + y * ref.src_pitch;
+        for (int64_t x = (int64_t)lane * V; x < w; x += 32 * V) {
+            uint32_t wa[NW];
+            load_px<V>(a + x, wa);
+            if constexpr (U8) {
+                uint32_t wb[NW];
+                load_px<V>(rec_u8 + y * rec_pitch + x, wb);
+                if constexpr (V >= 8) {
+                    unsigned aa = 0, bb = 0, ab = 0;  // at most 16 * 255^2 each
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int d = (int)a[k] - (int)b[k];
-                s += (unsigned)(d * d);
-            }
-            su += s;
-        } else {
-            const float *b = rec_f32 + y * rec_pitch_f32 + x;
-            float s = 0.0f;
+                    for (int k = 0; k < NW; ++k) {
+                        aa = __dp4a(wa[k], wa[k], aa);
+                        bb = __dp4a(wb[k], wb[k], bb);
+                        ab = __dp4a(wa[k], wb[k], ab);
+                    }
+                    su += (unsigned long long)aa + bb - 2ull * ab;
+                } else {
+                    const int d = (int)wa[0] - (int)wb[0];
+                    su += (unsigned)(d * d);
+                }
+            } else {
+                const float *b = rec_f32 + y * rec_pitch_f32 + x;
+                float s = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float d = b[k] - (float)a[k];
-                s = __fmaf_rn(d, d, s);
+                for (int k = 0; k < V; ++k) {
+                    const float d = b[k] - (float)((V >= 8) ? byte_of(wa[k >> 2], k & 3) : wa[0]);
+                    s = __fmaf_rn(d, d, s);
+                }
+                sf += (double)s;
             }
-            sf += (double)s;
         }
     }
-    const int lane = threadIdx.x & 31;
-    if (rec_u8) {
+    if constexpr (U8) {
         su = warp_sum_u64(su);
         if (lane == 0 && su) atomicAdd(acc_u64, su);
     } else {
@@ -269,7 +344,7 @@ static int grid_for(int64_t work_items, int threads, int ctas_per_sm = 4) {
 
 cudaError_t launch_forward(const JobDesc &job, int32_t *Y, cudaStream_t s) {
     const int64_t nb = (int64_t)job.nbw * job.nbh;
-    forward_kernel<<<grid_for(nb, 256, 8), 256, 0, s>>>(job, Y);
+    forward_kernel<<<grid_for(nb, kFwdWarps * 32, 8), kFwdWarps * 32, 0, s>>>(job, Y);
     return cudaGetLastError();
 }
 
@@ -277,8 +352,9 @@ cudaError_t launch_forward_f32(const JobDesc &job, int kind, float *Y, cudaStrea
     const int64_t nb = (int64_t)job.nbw * job.nbh;
     const DctConsts C = make_dct_consts();
     const ScaleConsts S = make_scale_consts();
-    if (kind == RDCT_KIND_RDCT) forward_f32_kernel<RDCT_KIND_RDCT><<<grid_for(nb, 256, 8), 256, 0, s>>>(job, Y, C, S);
-    else forward_f32_kernel<RDCT_KIND_DCT><<<grid_for(nb, 256, 8), 256, 0, s>>>(job, Y, C, S);
+    const int g = grid_for(nb, kFwdWarps * 32, 8);
+    if (kind == RDCT_KIND_RDCT) forward_f32_kernel<RDCT_KIND_RDCT><<<g, kFwdWarps * 32, 0, s>>>(job, Y, C, S);
+    else forward_f32_kernel<RDCT_KIND_DCT><<<g, kFwdWarps * 32, 0, s>>>(job, Y, C, S);
     return cudaGetLastError();
 }
 
@@ -288,24 +364,59 @@ cudaError_t launch_compress(const int32_t *Y, int64_t nblocks, int32_t r, float 
     return cudaGetLastError();
 }
 
+template <int KIND>
+static void launch_inverse_kind(int d, int g, const float *Yc, int64_t nbw, int64_t nbh, int32_t r, uint8_t *u8,
+                                int64_t pitch, int u8_align, float *f32, int64_t pitch_f32, const ScaleConsts &S,
+                                const DctConsts &C, cudaStream_t s) {
+    switch (d) {
+#define RDCT_ICASE(dd)                                                                                        \
+    case dd:                                                                                                  \
+        inverse_kernel<KIND, dd><<<g, 256, 0, s>>>(Yc, nbw, nbh, r, u8, pitch, u8_align, f32, pitch_f32, S, C); \
+        break;
+        RDCT_ICASE(0) RDCT_ICASE(1) RDCT_ICASE(2) RDCT_ICASE(3) RDCT_ICASE(4) RDCT_ICASE(5) RDCT_ICASE(6)
+        RDCT_ICASE(7) RDCT_ICASE(8) RDCT_ICASE(9) RDCT_ICASE(10) RDCT_ICASE(11) RDCT_ICASE(12) RDCT_ICASE(13)
+        RDCT_ICASE(14)
+#undef RDCT_ICASE
+        default: break;
+    }
+}
+
 cudaError_t launch_inverse(const float *Yc, int64_t nbw, int64_t nbh, int32_t r, int kind, uint8_t *u8, int64_t pitch,
                            float *f32, int64_t pitch_f32, cudaStream_t s) {
     const int64_t nb = nbw * nbh;
     const int g = grid_for(nb, 256, 8);
+    const int d = diag_class_host(r);
+    const uintptr_t ua = reinterpret_cast<uintptr_t>(u8);
+    const int u8_align = (ua % 8 == 0 && pitch % 8 == 0) ? 8 : 1;
     if (kind == RDCT_KIND_RDCT)
-        inverse_kernel<RDCT_KIND_RDCT><<<g, 256, 0, s>>>(Yc, nbw, nbh, r, u8, pitch, f32, pitch_f32,
-                                                         make_zigzag_table(), make_scale_consts(), DctConsts{});
+        launch_inverse_kind<RDCT_KIND_RDCT>(d, g, Yc, nbw, nbh, r, u8, pitch, u8_align, f32, pitch_f32,
+                                            make_scale_consts(), DctConsts{}, s);
     else
-        inverse_kernel<RDCT_KIND_DCT><<<g, 256, 0, s>>>(Yc, nbw, nbh, r, u8, pitch, f32, pitch_f32,
-                                                        make_zigzag_table(), ScaleConsts{}, make_dct_consts());
+        launch_inverse_kind<RDCT_KIND_DCT>(d, g, Yc, nbw, nbh, r, u8, pitch, u8_align, f32, pitch_f32, ScaleConsts{},
+                                           make_dct_consts(), s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sse(const JobDesc &ref, const uint8_t *rec_u8, int64_t rec_pitch, const float *rec_f32,
                        int64_t rec_pitch_f32, unsigned long long *acc_u64, double *acc_f64, cudaStream_t s) {
-    const int64_t groups = (int64_t)ref.nbw * ref.nbh * 8;
-    sse_kernel<<<grid_for(groups, 256, 8), 256, 0, s>>>(ref, rec_u8, rec_pitch, rec_f32, rec_pitch_f32, acc_u64,
-                                                         acc_f64);
+    const int64_t rows = (int64_t)ref.nbh * 8, w = (int64_t)ref.nbw * 8;
+    const int g = grid_for(rows * 32, 256, 8);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(ref.src);
+    const uintptr_t b = rec_u8 ? reinterpret_cast<uintptr_t>(rec_u8) : reinterpret_cast<uintptr_t>(rec_f32);
+    const int64_t bp = rec_u8 ? rec_pitch : rec_pitch_f32 * 4;
+    auto aligned = [&](int k) { return a % k == 0 && ref.src_pitch % k == 0 && (!rec_u8 || (b % k == 0 && bp % k == 0)); };
+    // a row is a multiple of 8 pixels; 16-pixel steps need a multiple of 16
+    const int V = (aligned(16) && w % 16 == 0) ? 16 : (aligned(8) ? 8 : 1);
+#define RDCT_SSE(v)                                                                                                \
+    do {                                                                                                           \
+        if (rec_u8) sse_kernel<v, true><<<g, 256, 0, s>>>(ref, rec_u8, rec_pitch, rec_f32, rec_pitch_f32, acc_u64,  \
+                                                          acc_f64);                                                \
+        else sse_kernel<v, false><<<g, 256, 0, s>>>(ref, rec_u8, rec_pitch, rec_f32, rec_pitch_f32, acc_u64, acc_f64); \
+    } while (0)
+    if (V == 16) RDCT_SSE(16);
+    else if (V == 8) RDCT_SSE(8);
+    else RDCT_SSE(1);
+#undef RDCT_SSE
     return cudaGetLastError();
 }
 

@@ -18,6 +18,13 @@
 
 namespace rdct {
 
+// Pixel n (0..3) of a packed word as an exact float without a conversion
+// instruction: the byte goes under the exponent of 2^23 (one byte permute)
+// and 2^23 is subtracted (one add), both on full-rate pipes.
+__device__ __forceinline__ float px_float(uint32_t w, int n) {
+    return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7540u + (unsigned)n)) - 8388608.0f;
+}
+
 template <int D>
 __device__ __forceinline__ float variant_block(const uint32_t w[16], int r, const MatConsts &M, uint8_t *dst,
                                                int64_t dpitch, int dalign, float *dstf, int64_t fpitch) {
@@ -29,8 +36,8 @@ __device__ __forceinline__ float variant_block(const uint32_t w[16], int r, cons
         float a[8];
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
-            a[n] = (float)byte_of(w[2 * i], n);
-            a[n + 4] = (float)byte_of(w[2 * i + 1], n);
+            a[n] = px_float(w[2 * i], n);
+            a[n + 4] = px_float(w[2 * i + 1], n);
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -83,7 +90,7 @@ __device__ __forceinline__ float variant_block(const uint32_t w[16], int r, cons
         }
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const float e = X[m] - (float)byte_of(w[2 * n + (m >> 2)], m & 3);
+            const float e = X[m] - px_float(w[2 * n + (m >> 2)], m & 3);
             sse = __fmaf_rn(e, e, sse);
         }
         if (dst != nullptr) {

@@ -134,7 +134,7 @@ def _tune(bpt):
 
 
 def test_dropped_coefficient_form_matches_the_scalar_kernel(dev):
-    """From r = 33 the two-block kernel rebuilds each block as 576 A - C0^T (W o Y_dropped) C0 from the
+    """From r = 36 the two-block kernel rebuilds each block as 576 A - C0^T (W o Y_dropped) C0 from the
     coefficients it drops; the scalar kernel still inverts the kept ones.  The two must agree bit for bit
     (reconstruction, exact SSE and the 8-bit error) at every r from 32 to 64, for planes that take TMA
     staging (16-byte aligned, full 32-column segments) and planes that take the per-thread copies (an

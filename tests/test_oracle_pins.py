@@ -280,6 +280,27 @@ def test_u8_output_is_rounded_clamped_reconstruction():
     assert xhat.min() < 0 and xhat.max() > 255  # both clamps are exercised
 
 
+def test_sse_hand_computed_on_padded_rows():
+    """The squared-error sum (Sec. 3) over a plane whose rows are padded: only the w x h window counts,
+    row by row.  Reference 10 everywhere and reconstruction 13 (9 per pixel) except three pixels set
+    apart so that a transposed or mis-pitched walk changes the sum; the padding holds values that
+    would dominate it if read."""
+    h, w, pitch = 16, 24, 40
+    ref_buf = np.full((h, pitch), 250, np.uint8)
+    rec_buf = np.full((h, pitch), 0, np.uint8)
+    ref, rec = ref_buf[:, :w], rec_buf[:, :w]
+    ref[...] = 10
+    rec[...] = 13
+    rec[2, 5] = 20    # (20 - 10)^2 = 100
+    rec[15, 23] = 0   # 100
+    ref[7, 0] = 200   # (13 - 200)^2 = 34969
+    expected = 9 * (h * w - 3) + 100 + 100 + 34969  # 38598
+    assert orc.sse(ref, rec) == 38598 == expected
+    # a float reconstruction 0.5 above: (d + 1/2)^2 = d^2 + d + 1/4, and the differences d sum to
+    # 3 * 381 + 10 - 10 - 187 = 956, so the sum is 38598 + 956 + 384 / 4 = 39650
+    assert orc.sse(ref, rec.astype(np.float64) + 0.5) == 39650.0
+
+
 def test_sweep_matches_fused_and_is_monotone():
     """The r sweep equals the fused error at each r, decreases with r, and is 0 at 64."""
     img = synth.image_1f(16, 24, seed=15)
