@@ -255,8 +255,13 @@ typedef struct {
                                 blocks_per_thread 2) */
     int32_t items_per_chunk; /* work items handed to a warp at a time (an item is one row of 32
                                 lanes' blocks or block pairs) */
-    int32_t blocks_per_thread; /* 2: dp4a/f32x2 kernel, two vertically adjacent 8x8 blocks per
-                                  thread, 4 warps per CTA; 1: scalar kernel, one block per thread */
+    int32_t blocks_per_thread; /* 2: two-block kernel (packed integer forward, f32x2 inverse), two
+                                  vertically adjacent 8x8 blocks per thread, 4 warps per CTA;
+                                  1: scalar kernel, one block per thread */
+    int32_t staging;           /* blocks_per_thread 2 only.  0: TMA tile staging for the planes and r
+                                  where it pays (16-byte aligned planes, r >= 16, nearly full
+                                  32-column segments), per-thread copies elsewhere; 1: per-thread
+                                  copies for every plane */
 } rdct_tune;
 
 typedef struct rdct_plan rdct_plan;
@@ -292,9 +297,14 @@ RDCT_API rdct_status rdct_batch_plan_get_tune(const rdct_plan *plan, rdct_tune *
 RDCT_API rdct_status rdct_batch_plan_kernels(const rdct_plan *plan, int32_t *kernels_per_run);
 RDCT_API rdct_status rdct_batch_plan_destroy(rdct_plan *plan);
 
-/* Time candidate launch shapes on this batch (CUDA events, repeated runs)
- * and return the fastest in *best; the result is also kept in a per-process
- * cache keyed by the batch's shape class. */
+/* Time candidate launch shapes on this batch and return the fastest in
+ * *best; the result is also kept in a per-process cache keyed by the batch's
+ * shape class.  Candidates: the two-block kernel at 0 / 3 / 4 CTAs per SM,
+ * 4..32 items per chunk, with and without TMA staging, and the scalar kernel.
+ * Each is run once to capture and warm its graph, then timed over repeated
+ * runs (CUDA events); a candidate whose runs spread by more than 5% is timed
+ * again, and dropped if it stays that noisy.  The default shape is kept
+ * unless a candidate's median beats it by more than 1%. */
 RDCT_API rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, rdct_tune *best, rdct_stream stream);
 
 /* -------------------------------------------- host-resident streaming path */

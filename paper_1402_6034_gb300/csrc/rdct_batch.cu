@@ -69,15 +69,23 @@ rdct_tune default_tune() {
     t.ctas_per_sm = 0;  // occupancy limit
     t.items_per_chunk = 16;
     t.blocks_per_thread = 2;
+    t.staging = 0;
     return t;
 }
 
 rdct_status validate_tune(const rdct_tune &t) {
     if (t.warps_per_cta < 1 || t.warps_per_cta > 8 || t.ctas_per_sm < 0 || t.ctas_per_sm > 64 ||
-        t.items_per_chunk < 1 || t.items_per_chunk > 4096 || (t.blocks_per_thread != 1 && t.blocks_per_thread != 2))
+        t.items_per_chunk < 1 || t.items_per_chunk > 4096 || (t.blocks_per_thread != 1 && t.blocks_per_thread != 2) ||
+        (t.staging != 0 && t.staging != 1))
         return set_error(RDCT_ERR_ARG, "rdct_tune: out of range (warps 1..8, ctas_per_sm 0..64, "
-                                       "items_per_chunk 1..4096, blocks_per_thread 1 or 2)");
+                                       "items_per_chunk 1..4096, blocks_per_thread 1 or 2, staging 0 or 1)");
     return RDCT_OK;
+}
+
+bool same_tune(const rdct_tune &a, const rdct_tune &b) {
+    return a.warps_per_cta == b.warps_per_cta && a.ctas_per_sm == b.ctas_per_sm &&
+           a.items_per_chunk == b.items_per_chunk && a.blocks_per_thread == b.blocks_per_thread &&
+           a.staging == b.staging;
 }
 
 rdct_status validate_jobs(const rdct_job *jobs, int32_t njobs, int32_t nimages) {
@@ -108,7 +116,7 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     }
     // TMA staging per job: two blocks per thread, an r where it pays, and a
     // plane (and reconstruction) whose tensor maps encode
-    const bool tma_ok = p->tune.blocks_per_thread == 2 && njobs > 0 && tma_available();
+    const bool tma_ok = p->tune.blocks_per_thread == 2 && p->tune.staging == 0 && njobs > 0 && tma_available();
     p->job_tma.assign(njobs, 0);
     p->maps.clear();
     p->tma = false;
@@ -334,22 +342,51 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
         cudaFree(sse);
         return set_error(RDCT_ERR_CUDA, "rdct_autotune: event creation failed");
     }
-    std::vector<rdct_tune> cands;
-    // blocks_per_thread 2: the dp4a/f32x2 kernel (fixed 4 warps); 1: the scalar kernel
-    for (int bpt : {2, 1})
-        for (int ctas : {0, 2, 4})
-            for (int items : {2, 4, 8, 16, 32}) {
-                rdct_tune t{};
-                t.warps_per_cta = bpt == 2 ? 4 : 8;
+    // the default first, so that every other candidate is measured against it
+    std::vector<rdct_tune> cands{default_tune()};
+    for (int staging : {0, 1})
+        for (int ctas : {0, 3, 4})
+            for (int items : {4, 8, 16, 32}) {
+                rdct_tune t = default_tune();
                 t.ctas_per_sm = ctas;
                 t.items_per_chunk = items;
-                t.blocks_per_thread = bpt;
-                cands.push_back(t);
+                t.staging = staging;
+                if (!same_tune(t, cands[0])) cands.push_back(t);
             }
-    float best_ms = 1e30f;
+    for (int items : {8, 16}) {  // the scalar kernel (one block per thread)
+        rdct_tune t = default_tune();
+        t.warps_per_cta = 8;
+        t.blocks_per_thread = 1;
+        t.items_per_chunk = items;
+        cands.push_back(t);
+    }
+    // median of `reps` timed runs; a candidate whose runs spread by more than
+    // 5% is measured once more, and dropped if it is still that noisy
+    auto measure = [&](rdct_plan *p, float *median) -> bool {
+        constexpr int reps = 5;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            std::vector<float> t;
+            for (int k = 0; k < reps; ++k) {
+                cudaEventRecord(e0, s);
+                if (rdct_batch_run(p, sse, nullptr, s) != RDCT_OK) return false;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t.push_back(ms);
+            }
+            std::sort(t.begin(), t.end());
+            *median = t[reps / 2];
+            if (t.back() <= 1.05f * t.front()) return true;
+        }
+        *median = -1.0f;  // too noisy to rank
+        return true;
+    };
+    float best_ms = 1e30f, default_ms = -1.0f;
     rdct_tune best_t = default_tune();
     rdct_status result = RDCT_OK;
-    for (const rdct_tune &t : cands) {
+    for (size_t c = 0; c < cands.size(); ++c) {
+        const rdct_tune &t = cands[c];
         rdct_plan *p = nullptr;
         st = rdct_batch_plan_create(jobs, njobs, nimages, &t, &p);
         if (st) {
@@ -357,25 +394,16 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
             break;
         }
         bool ok = rdct_batch_run(p, sse, nullptr, s) == RDCT_OK;  // capture + warm-up
-        const int reps = 3;
-        std::vector<float> times;
-        for (int k = 0; k < reps && ok; ++k) {
-            cudaEventRecord(e0, s);
-            ok = rdct_batch_run(p, sse, nullptr, s) == RDCT_OK;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            times.push_back(ms);
-        }
+        ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+        float med = -1.0f;
+        ok = ok && measure(p, &med);
         rdct_batch_plan_destroy(p);
         if (!ok) {
             result = set_error(RDCT_ERR_CUDA, "rdct_autotune: a candidate failed to run");
             break;
         }
-        std::sort(times.begin(), times.end());
-        const float med = times[times.size() / 2];
-        if (med < best_ms) {
+        if (c == 0) default_ms = med;
+        if (med > 0.0f && med < best_ms) {
             best_ms = med;
             best_t = t;
         }
@@ -384,6 +412,8 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
     cudaEventDestroy(e1);
     cudaFree(sse);
     if (result != RDCT_OK) return result;
+    // keep the default unless a candidate is clearly faster
+    if (default_ms > 0.0f && best_ms > 0.99f * default_ms) best_t = default_tune();
     *best = best_t;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[shape_key(jobs, njobs)] = best_t;

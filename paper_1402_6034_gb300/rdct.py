@@ -49,7 +49,8 @@ class Job(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("items_per_chunk", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32)]
+                ("items_per_chunk", ctypes.c_int32), ("blocks_per_thread", ctypes.c_int32),
+                ("staging", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -395,7 +396,7 @@ class BatchPlan:
         t = None
         if tune is not None:
             t = Tune(tune["warps_per_cta"], tune["ctas_per_sm"], tune["items_per_chunk"],
-                     tune.get("blocks_per_thread", 1))
+                     tune.get("blocks_per_thread", 1), tune.get("staging", 0))
         h = ctypes.c_void_p()
         _check(load().rdct_batch_plan_create(arr, len(jobs), nimages, ctypes.byref(t) if t else None, ctypes.byref(h)),
                "rdct_batch_plan_create")

@@ -68,7 +68,10 @@ def test_validation_happens_before_any_launch():
     job = rdct.Job(ok, None, 0, 10, 5)  # image index out of range
     plan = ctypes.c_void_p()
     assert lib.rdct_batch_plan_create((rdct.Job * 1)(job), 1, 2, None, ctypes.byref(plan)) == 1
-    tune = rdct.Tune(64, 0, 8, 2)  # too many warps
+    tune = rdct.Tune(64, 0, 8, 2, 0)  # too many warps
+    job = rdct.Job(ok, None, 0, 10, 0)
+    assert lib.rdct_batch_plan_create((rdct.Job * 1)(job), 1, 1, ctypes.byref(tune), ctypes.byref(plan)) == 1
+    tune = rdct.Tune(4, 0, 8, 2, 2)  # unknown staging
     job = rdct.Job(ok, None, 0, 10, 0)
     assert lib.rdct_batch_plan_create((rdct.Job * 1)(job), 1, 1, ctypes.byref(tune), ctypes.byref(plan)) == 1
     opts = rdct.ServerOpts(1024, 1, 1, 1, 0)  # budget below 1 MiB

@@ -127,6 +127,18 @@ def test_batch_mixed_staging(dev):
     for a, j in zip(outs, jobs):
         if a is not None:
             assert torch.equal(a, j.dst)
+    # the same plan with per-thread copies for every plane (tune staging 1): no TMA launch, same results
+    plan_c = rdct.BatchPlan(jobs, len(shapes), tune={"warps_per_cta": 4, "ctas_per_sm": 0, "items_per_chunk": 16,
+                                                     "blocks_per_thread": 2, "staging": 1})
+    assert plan_c.kernels_per_run() == nr + 1
+    sse_c = torch.empty(len(shapes), dtype=torch.float64, device=dev)
+    plan_c.run(sse_c)
+    rdct.sync()
+    plan_c.close()
+    assert torch.equal(sse, sse_c)
+    for a, j in zip(outs, jobs):
+        if a is not None:
+            assert torch.equal(a, j.dst)
 
 
 def _tune(bpt):
@@ -216,7 +228,7 @@ def test_batch_equals_per_plane(dev):
 def test_autotune_picks_a_valid_shape(dev):
     specs, jobs, host = _batch(dev, n_images=8, seed=11)
     t = rdct.autotune(jobs, len(specs))
-    assert 1 <= t["warps_per_cta"] <= 32 and t["items_per_chunk"] >= 1
+    assert 1 <= t["warps_per_cta"] <= 32 and t["items_per_chunk"] >= 1 and t["staging"] in (0, 1)
     plan = rdct.BatchPlan(jobs, len(specs))  # picks the cached tune
     assert plan.tune == t
     sse = torch.empty(len(specs), dtype=torch.float64, device=dev)

@@ -7,11 +7,17 @@ whose host process forbids device allocation.  rdct_sweep_noalloc keeps its
 tables in a fixed device array inside the library instead.  This file checks,
 through the C-ABI, that two calls in a row give the same results as
 rdct_sweep (the second call with different planes, so stale tables from the
-first would show) and that oversized calls are refused.
+first would show), that oversized calls are refused, and that a call really
+takes no memory from the device's stream-ordered pool (where rdct_sweep takes
+its tables) and leaves the free device memory unchanged.
 
 It sits in its own file, collected last, and passes both alone in a fresh
 process and after the other tests.
 """
+import ctypes
+import glob
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -62,3 +68,64 @@ def test_noalloc_rejects_oversized_calls(dev):
     with pytest.raises(rdct.RdctError) as e:
         rdct.sweep_noalloc([tall] * 2048, out2)
     assert e.value.status == 4
+
+
+def _cudart():
+    """The CUDA runtime as a shared library (for the memory-pool counters; the library under test
+    links its own copy, and both see the same device pool)."""
+    cands = []
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d:
+            cands += sorted(glob.glob(os.path.join(d, "lib64", "libcudart.so*")))
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    pytest.skip("libcudart not found")
+
+
+class _PoolHigh:
+    """High-water mark of the current device's default memory pool (cudaMemPoolAttrUsedMemHigh)."""
+
+    USED_MEM_HIGH = 8
+
+    def __init__(self):
+        self.rt = _cudart()
+        dev = ctypes.c_int()
+        assert self.rt.cudaGetDevice(ctypes.byref(dev)) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.rt.cudaDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def reset(self):
+        zero = ctypes.c_uint64(0)
+        assert self.rt.cudaMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+    def high(self) -> int:
+        v = ctypes.c_uint64()
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+
+def test_noalloc_takes_no_device_memory(dev):
+    planes = _planes(dev, [(512, 512), (256, 1024)], seed=70)
+    arr = rdct.plane_array(planes)
+    out = torch.zeros((len(planes), 64), dtype=torch.float64, device=dev)
+    rdct.sweep_noalloc(arr, out)  # warm: the first call on a device looks up the array's address
+    torch.cuda.synchronize()
+    pool = _PoolHigh()
+    # control: rdct_sweep takes its tables from the stream-ordered pool
+    pool.reset()
+    rdct.sweep(planes)
+    torch.cuda.synchronize()
+    assert pool.high() > 0
+    # the allocation-free call takes nothing from it, and the free device memory does not move
+    torch.cuda.synchronize()
+    pool.reset()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rdct.sweep_noalloc(arr, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert pool.high() == 0
+    assert free1 == free0
