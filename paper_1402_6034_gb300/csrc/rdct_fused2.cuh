@@ -82,6 +82,14 @@ __device__ __forceinline__ int dp4a_us(unsigned a, unsigned b, int c) {
     asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
     return d;
 }
+// The same with b a compile-time constant, given to the instruction as an
+// immediate operand (no register has to hold it).
+template <unsigned B>
+__device__ __forceinline__ int dp4a_us_imm(unsigned a, int c) {
+    int d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "n"(B), "r"(c));
+    return d;
+}
 // Weight group of W_ij (six distinct values).
 __host__ __device__ constexpr int weight_group(int i, int j) {
     const int w = weight(i, j);
@@ -135,11 +143,12 @@ __host__ __device__ constexpr bool drop_form(int R) { return R > 35; }
 // the column pass the 22-addition butterfly in int32.
 __device__ __forceinline__ void forward_c0_int(const uint2 (&w)[8], int (&Y)[8][8]) {
     int R[8][8];
+    static_for<0, 8>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            R[i][k] = dp4a_us(w[i].x, c0_row_word(k, 0), dp4a_us(w[i].y, c0_row_word(k, 1), 0));
+        for (int i = 0; i < 8; ++i)
+            R[i][k] = dp4a_us_imm<c0_row_word(k, 0)>(w[i].x, dp4a_us_imm<c0_row_word(k, 1)>(w[i].y, 0));
+    });
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int c[8], o[8];

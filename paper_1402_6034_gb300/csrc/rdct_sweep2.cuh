@@ -28,41 +28,69 @@ static_assert(kSweepChunkStrips * kFusedVRows * 16320ull * 16320ull < (1ull << 3
 // row on the packed pixels), then the column butterfly, then its eight
 // energies; only eight intermediates are live next to the 64 bins.
 __device__ __forceinline__ void sweep_rdct_block(const uint2 (&w)[8], unsigned (&bins)[64]) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    static_for<0, 8>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
         int c[8], o[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) c[i] = dp4a_us(w[i].x, c0_row_word(j, 0), dp4a_us(w[i].y, c0_row_word(j, 1), 0));
+        for (int i = 0; i < 8; ++i)
+            c[i] = dp4a_us_imm<c0_row_word(j, 0)>(w[i].x, dp4a_us_imm<c0_row_word(j, 1)>(w[i].y, 0));
         c0_forward(c, o);
 #pragma unroll
         for (int i = 0; i < 8; ++i) bins[i * 8 + j] += (unsigned)(o[i] * o[i]);
-    }
+    });
 }
 
-// 8-point orthonormal DCT of an f32x2 pair of vectors (even/odd split, FMAs
-// with the FP32 cos constants, each constant used for both halves).
-__device__ __forceinline__ void dct8_f2(const f2 (&x)[8], f2 (&X)[8], const DctConsts &C) {
+// The constants of the factored 8-point DCT as f32x2 pairs (c, c), built once
+// per thread and kept in registers: s = C[0][0] = C[4][0] (sqrt(1/8)),
+// c_m = C[1][.] and C[2][.] entries = cos(m pi / 16) / 2, and the negatives
+// the odd rows need.
+struct DctPairs {
+    f2 s, c2, c6, nc2, c1, c3, c5, c7, nc1, nc5, nc7;
+};
+__device__ __forceinline__ DctPairs dct_pairs(const DctConsts &C) {
+    auto p = [](float v) { return f2_make(v, v); };
+    DctPairs d;
+    d.s = p(C.c[0]);
+    d.c2 = p(C.c[16]);
+    d.c6 = p(C.c[17]);
+    d.nc2 = p(-C.c[16]);
+    d.c1 = p(C.c[8]);
+    d.c3 = p(C.c[9]);
+    d.c5 = p(C.c[10]);
+    d.c7 = p(C.c[11]);
+    d.nc1 = p(-C.c[8]);
+    d.nc5 = p(-C.c[10]);
+    d.nc7 = p(-C.c[11]);
+    return d;
+}
+
+// 8-point orthonormal DCT of an f32x2 pair of vectors, factored by the
+// symmetries of C (rows 2k even about the centre, rows 2k+1 odd, and rows 0,
+// 4, 2, 6 again even / odd on the half sums): 36 f32x2 operations with 11
+// constant pairs held in registers.
+__device__ __forceinline__ void dct8_f2_factored(const f2 (&x)[8], f2 (&X)[8], const DctPairs &K) {
     f2 a[4], b[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         a[n] = x[n] + x[7 - n];
         b[n] = x[n] - x[7 - n];
     }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const f2(&v)[4] = (k & 1) ? b : a;
-        f2 acc = mul2(f2_make(C.c[k * 8], C.c[k * 8]), v[0]);
-#pragma unroll
-        for (int n = 1; n < 4; ++n) acc = fma2(f2_make(C.c[k * 8 + n], C.c[k * 8 + n]), v[n], acc);
-        X[k] = acc;
-    }
+    const f2 e03 = a[0] + a[3], e12 = a[1] + a[2], d03 = a[0] - a[3], d12 = a[1] - a[2];
+    X[0] = mul2(K.s, e03 + e12);
+    X[4] = mul2(K.s, e03 - e12);
+    X[2] = fma2(K.c2, d03, mul2(K.c6, d12));
+    X[6] = fma2(K.c6, d03, mul2(K.nc2, d12));
+    X[1] = fma2(K.c7, b[3], fma2(K.c5, b[2], fma2(K.c3, b[1], mul2(K.c1, b[0]))));
+    X[3] = fma2(K.nc5, b[3], fma2(K.nc1, b[2], fma2(K.nc7, b[1], mul2(K.c3, b[0]))));
+    X[5] = fma2(K.c3, b[3], fma2(K.c7, b[2], fma2(K.nc1, b[1], mul2(K.c5, b[0]))));
+    X[7] = fma2(K.nc1, b[3], fma2(K.c3, b[2], fma2(K.nc5, b[1], mul2(K.c7, b[0]))));
 }
 
 // Exact DCT energies of one block with f32x2 arithmetic: the row pass runs on
 // pairs of rows, the column pass on pairs of columns.  Pixels become floats
 // by placing each byte under the exponent of 2^23 (a byte permute) and
 // subtracting 2^23, exactly.
-__device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctConsts &C) {
+__device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bins)[64], const DctPairs &C) {
     const f2 two23 = f2_make(8388608.0f, 8388608.0f);
     float R[8][8];
 #pragma unroll
@@ -76,7 +104,7 @@ __device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bin
             x[n + 4] = f2_make(__int_as_float((int)__byte_perm(w[i].y, 0x4B000000u, sel)),
                                __int_as_float((int)__byte_perm(w[i + 1].y, 0x4B000000u, sel))) - two23;
         }
-        dct8_f2(x, X, C);
+        dct8_f2_factored(x, X, C);
 #pragma unroll
         for (int k = 0; k < 8; ++k) f2_split(X[k], R[i][k], R[i + 1][k]);
     }
@@ -85,7 +113,7 @@ __device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bin
         f2 c[8], o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) c[i] = f2_make(R[i][j], R[i][j + 1]);
-        dct8_f2(c, o, C);
+        dct8_f2_factored(c, o, C);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float y0, y1;
@@ -138,6 +166,7 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
         ub[p] = 0u;
         fb[p] = 0.0f;
     }
+    const DctPairs K = dct_pairs(C);
     Cursor fc{gw, 0, 0, 0, 0, 0};
     cursor_load<false>(a, fc, lane);
     Cursor cc = fc;
@@ -172,7 +201,7 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
 #pragma unroll
                 for (int i = 0; i < 8; ++i) w[i] = ring[((stage * kVRows + v) * 8 + i) * THREADS + threadIdx.x];
                 if constexpr (KIND == RDCT_KIND_RDCT) sweep_rdct_block(w, ub);
-                else sweep_dct_block(w, fb, C);
+                else sweep_dct_block(w, fb, K);
             }
         }
         stage = stage + 1 == kStages ? 0 : stage + 1;
