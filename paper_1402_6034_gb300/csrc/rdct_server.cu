@@ -33,6 +33,10 @@
 #include <thread>
 #include <vector>
 
+#if defined(__linux__)
+#include <sys/prctl.h>
+#endif
+
 #include "rdct_device.cuh"
 #include "rdct_internal.h"
 
@@ -42,6 +46,9 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 constexpr int kServerItemsPerChunk = 8;
+// Interval at which the scheduler polls the completion events of launches in
+// flight (it wakes at once for new requests).
+constexpr int kPollUs = 10;
 
 struct Req {
     uint64_t ticket = 0;
@@ -212,6 +219,12 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
 
 void scheduler(rdct_server *S) {
     cudaSetDevice(S->device);
+#if defined(PR_SET_TIMERSLACK)
+    // The loop polls in-flight launches every few microseconds; with the default
+    // timer slack of an ordinary thread (50 us on Linux) each short timed wait
+    // could oversleep by that much and delay every completion.
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
         bool inflight = false;
@@ -311,7 +324,7 @@ void scheduler(rdct_server *S) {
         // 4. wait for the next event: new requests, or poll in-flight work
         bool busy = false;
         for (Lane &L : S->lanes) busy |= L.busy;
-        if (busy) S->cv_sched.wait_for(lk, std::chrono::microseconds(20));
+        if (busy) S->cv_sched.wait_for(lk, std::chrono::microseconds(kPollUs));
         else if (!S->ready.empty() || (!S->queue.empty() && S->fail_allocs == 0))
             S->cv_sched.wait_for(lk, std::chrono::microseconds(20));
         else if (!S->queue.empty())
