@@ -19,10 +19,39 @@
 
 namespace rdct {
 
-// Strips per sweep chunk (kSweepChunkStrips): a thread adds at most
-// 2 * 8 = 16 blocks into a 32-bit bin before the flush, and one block adds at
-// most 16320^2 < 2^28 to a bin, so 16 blocks fit.
-static_assert(kSweepChunkStrips * kFusedVRows * 16320ull * 16320ull < (1ull << 32), "sweep bins overflow");
+// The DC energy is never needed (every r keeps the DC coefficient), so the
+// bins hold AC energies only.  Every AC row of C0 sums to zero, so an AC
+// coefficient is sum k a with sum k = 0 and entries of k in {-1, 0, 1}, at
+// most 32 of them +1: |Y_ij| <= 32 * 255 = 8160 and Y^2 < 2^26.  A thread
+// adds kFusedVRows blocks per strip and kSweepChunkStrips strips per chunk,
+// and flushes its 32-bit bins at the latest after kSweepFlushChunks chunks:
+constexpr int kSweepFlushChunks = 4;
+static_assert(kSweepFlushChunks * kSweepChunkStrips * kFusedVRows * 8160ull * 8160ull < (1ull << 32),
+              "sweep bins overflow");
+// (the largest AC coefficient, for the bound above)
+__host__ __device__ constexpr int max_ac_coefficient() {
+    int m = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            if (i == 0 && j == 0) continue;
+            int pos = 0;
+            for (int y = 0; y < 8; ++y)
+                for (int x = 0; x < 8; ++x) pos += c0_entry(i, y) * c0_entry(j, x) > 0 ? 1 : 0;
+            m = pos > m ? pos : m;
+        }
+    return 255 * m;
+}
+static_assert(max_ac_coefficient() <= 8160, "AC coefficient bound");
+// zigzag rank of bin p = 8 i + j (for the flush's per-lane atomics)
+struct ZzRanks {
+    unsigned char r[64];
+};
+constexpr ZzRanks make_zz_ranks() {
+    ZzRanks t{};
+    for (int p = 0; p < 64; ++p) t.r[p] = (unsigned char)zz_rank(p >> 3, p & 7);
+    return t;
+}
+__constant__ ZzRanks kSweepZz = make_zz_ranks();
 
 // One output column at a time: column j of C0 A (the row pass, two dp4a per
 // row on the packed pixels), then the column butterfly, then its eight
@@ -36,7 +65,8 @@ __device__ __forceinline__ void sweep_rdct_block(const uint2 (&w)[8], unsigned (
             c[i] = dp4a_us_imm<c0_row_word(j, 0)>(w[i].x, dp4a_us_imm<c0_row_word(j, 1)>(w[i].y, 0));
         c0_forward(c, o);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) bins[i * 8 + j] += (unsigned)(o[i] * o[i]);
+        for (int i = 0; i < 8; ++i)
+            if (i + j > 0) bins[i * 8 + j] += (unsigned)(o[i] * o[i]);
     });
 }
 
@@ -118,7 +148,7 @@ __device__ __forceinline__ void sweep_dct_block(const uint2 (&w)[8], float (&bin
         for (int i = 0; i < 8; ++i) {
             float y0, y1;
             f2_split(o[i], y0, y1);
-            bins[i * 8 + j] = __fmaf_rn(y0, y0, bins[i * 8 + j]);
+            if (i + j > 0) bins[i * 8 + j] = __fmaf_rn(y0, y0, bins[i * 8 + j]);
             bins[i * 8 + j + 1] = __fmaf_rn(y1, y1, bins[i * 8 + j + 1]);
         }
     }
@@ -132,33 +162,59 @@ __device__ __forceinline__ unsigned long long warp_sum_u32_wide(unsigned v) {
     return ((unsigned long long)hi << 16) + lo;
 }
 
+// The warp's 63 AC bins into the plane's zigzag bins: each bin summed over the
+// warp, lane l keeping the totals of bins l and 32 + l, then two atomics per
+// lane.
 template <int KIND>
 __device__ __forceinline__ void sweep_flush(double *plane_bins, unsigned (&ub)[64], float (&fb)[64], int lane) {
+    unsigned long long u0 = 0ull, u1 = 0ull;
+    float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
-    for (int p = 0; p < 64; ++p) {
-        const int k = zz_rank(p >> 3, p & 7);
+    for (int p = 1; p < 64; ++p) {
         if constexpr (KIND == RDCT_KIND_RDCT) {
             const unsigned long long s = warp_sum_u32_wide(ub[p]) * (unsigned)weight(p >> 3, p & 7);
-            if (lane == (p & 31) && s) atomicAdd(reinterpret_cast<unsigned long long *>(plane_bins) + k, s);
+            if (lane == (p & 31)) {
+                if (p < 32) u0 = s;
+                else u1 = s;
+            }
             ub[p] = 0u;
         } else {
             const float s = warp_sum_f32(fb[p]);
-            if (lane == (p & 31) && s != 0.0f) atomicAdd(plane_bins + k, (double)s);
+            if (lane == (p & 31)) {
+                if (p < 32) f0 = s;
+                else f1 = s;
+            }
             fb[p] = 0.0f;
         }
+    }
+    const int k0 = kSweepZz.r[lane], k1 = kSweepZz.r[32 + lane];
+    if constexpr (KIND == RDCT_KIND_RDCT) {
+        unsigned long long *b = reinterpret_cast<unsigned long long *>(plane_bins);
+        if (u0) atomicAdd(b + k0, u0);
+        if (u1) atomicAdd(b + k1, u1);
+    } else {
+        if (f0 != 0.0f) atomicAdd(plane_bins + k0, (double)f0);
+        if (f1 != 0.0f) atomicAdd(plane_bins + k1, (double)f1);
     }
 }
 
 // Persistent sweep kernel over a chunk table (job = plane; out = [planes][64]
-// zigzag-ordered bins: uint64 576-scaled energies for RDCT, double for DCT).
+// zigzag-ordered bins: uint64 576-scaled energies for RDCT, double for DCT;
+// the DC bin stays 0).  Each warp takes a contiguous run of chunks, so that
+// consecutive chunks mostly belong to one plane and the bins are flushed only
+// when the plane changes or after kSweepFlushChunks chunks.
 template <int KIND>
-__global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_kernel(const Fused2Args a, double *out,
-                                                                                   const DctConsts C) {
+__global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_kernel(const Fused2Args args,
+                                                                                   double *out, const DctConsts C) {
     constexpr int THREADS = 128;
     __shared__ uint2 ring[kStages * 8 * kVRows * THREADS];
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    // this warp's chunks [c0, c1): the cursors step by one chunk and stop at c1
+    Fused2Args a = args;
+    const int gw = (int)((int64_t)warp * args.nchunks / nwarps);
+    a.nchunks = (int)((int64_t)(warp + 1) * args.nchunks / nwarps);
     unsigned ub[64];
     float fb[64];
 #pragma unroll
@@ -174,12 +230,12 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
     for (int s = 0; s < kStages - 1; ++s) {
         if (fc.c < a.nchunks) {
             fetch_strip<THREADS>(a.jobs[fc.job], fc.rp, fc.bx, ring, s);
-            cursor_next<false>(a, fc, nwarps, lane);
+            cursor_next<false>(a, fc, 1, lane);
         } else {
             cp_async_commit();
         }
     }
-    int stage = 0;
+    int stage = 0, since_flush = 0;
     while (cc.c < a.nchunks) {
         cp_async_wait<kStages - 2>();
         const JobDesc &job = a.jobs[cc.job];
@@ -188,7 +244,7 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
         const int refill = stage == 0 ? kStages - 1 : stage - 1;
         if (fc.c < a.nchunks) {
             fetch_strip<THREADS>(a.jobs[fc.job], fc.rp, fc.bx, ring, refill);
-            cursor_next<false>(a, fc, nwarps, lane);
+            cursor_next<false>(a, fc, 1, lane);
         } else {
             cp_async_commit();
         }
@@ -207,8 +263,13 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
         stage = stage + 1 == kStages ? 0 : stage + 1;
         const int plane = cc.job;
         const int cprev = cc.c;
-        cursor_next<false>(a, cc, nwarps, lane);
-        if (cc.c != cprev) sweep_flush<KIND>(out + (int64_t)plane * 64, ub, fb, lane);
+        cursor_next<false>(a, cc, 1, lane);
+        if (cc.c != cprev) {
+            if (++since_flush == kSweepFlushChunks || cc.c >= a.nchunks || cc.job != plane) {
+                sweep_flush<KIND>(out + (int64_t)plane * 64, ub, fb, lane);
+                since_flush = 0;
+            }
+        }
     }
     cp_async_wait<0>();
 }
