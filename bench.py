@@ -474,8 +474,8 @@ def bench_sweep(args, dev):
                        "samples_per_step": total, "note": "one pass per transform, 1 B/px read"},
             "roofline": {"bound": "hbm", "achieved": total / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": total / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{kind} hbm_gbs",
-                         "limiter": "instruction issue, not DRAM: both passes need all 64 coefficients of every "
-                                    "block (ncu: about 62 % of issue slots busy, DRAM read 2.4 and 1.6 TB/s)"},
+                         "limiter": "instruction issue, not DRAM: both passes need all 63 AC coefficients of "
+                                    "every block (ncu: 63-66 % of issue slots busy, DRAM read 3.0 and 1.9 TB/s)"},
             "gpu_launches": 6 * args.steps, "per_r": rows,
             "uqi_kernel": {"image": "512x512 u8", "us": uqi_ms * 1e3,
                            "windows_per_s": 505 * 505 / (uqi_ms / 1e3), "uqi_subset_images": n_uqi}}
