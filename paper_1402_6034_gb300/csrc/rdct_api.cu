@@ -274,8 +274,7 @@ rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, doub
         return set_error(RDCT_ERR_OOM, "rdct_sweep: table allocation failed");
     JobDesc *jd = reinterpret_cast<JobDesc *>(tables);
     Chunk *cd = reinterpret_cast<Chunk *>(reinterpret_cast<char *>(tables) + jb);
-    cudaError_t e = build_sweep_tables(planes, n, jd, cd, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sse_by_r, 0, (size_t)n * 64 * sizeof(double), s);
+    cudaError_t e = build_sweep_tables(planes, n, jd, cd, sse_by_r, s);
     if (e == cudaSuccess) e = launch_sweep(jd, cd, (int32_t)nchunks, (int)kind, sse_by_r, n, s);
     if (e == cudaSuccess) e = launch_sweep_finalize(sse_by_r, n, (int)kind, s);
     cudaError_t e2 = cudaFreeAsync(tables, s);

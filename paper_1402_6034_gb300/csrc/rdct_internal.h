@@ -169,7 +169,9 @@ cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchu
 // parameters (batches of kSweepBuildBatch planes; no host-to-device copy).
 constexpr int kSweepBuildBatch = 1024;
 int64_t sweep_chunk_count(const rdct_plane &p);
-cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, cudaStream_t s);
+// (also clears out: the planes' 64 bins each)
+cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, double *out,
+                               cudaStream_t s);
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
                          int32_t nplanes, cudaStream_t s);
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s);

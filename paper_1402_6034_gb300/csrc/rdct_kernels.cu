@@ -301,6 +301,8 @@ __global__ void mse_finalize_kernel(const unsigned long long *acc_u64, const dou
 // One warp per plane: lane l holds bins 2l and 2l+1; a suffix scan over the
 // warp gives every tail sum.
 __global__ void sweep_finalize_kernel(double *out, int32_t nplanes, int kind) {
+    // launched as a programmatic dependent of the sweep kernel
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= nplanes) return;
@@ -441,8 +443,16 @@ cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchun
 
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s) {
     if (nplanes <= 0) return cudaSuccess;
-    sweep_finalize_kernel<<<(nplanes + 3) / 4, 128, 0, s>>>(out, nplanes, kind);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((nplanes + 3) / 4));
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_finalize_kernel, out, nplanes, kind);
 }
 
 }  // namespace rdct

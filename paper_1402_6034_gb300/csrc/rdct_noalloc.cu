@@ -91,9 +91,8 @@ extern "C" rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, r
     Chunk *d_chunks = reinterpret_cast<Chunk *>(base + kChunksOff);
     cudaStream_t s = (cudaStream_t)stream;
     // the tables are rewritten in full by every call (from plane descriptors
-    // passed as kernel parameters); only the output bins must start at zero
-    RDCT_CUDA_TRY(build_sweep_tables(planes, n, d_jobs, d_chunks, s));
-    RDCT_CUDA_TRY(cudaMemsetAsync(sse_by_r, 0, (size_t)n * 64 * sizeof(double), s));
+    // passed as kernel parameters), and the same kernel clears the output bins
+    RDCT_CUDA_TRY(build_sweep_tables(planes, n, d_jobs, d_chunks, sse_by_r, s));
     RDCT_CUDA_TRY(launch_sweep(d_jobs, d_chunks, (int32_t)nchunks, (int)kind, sse_by_r, n, s));
     RDCT_CUDA_TRY(launch_sweep_finalize(sse_by_r, n, (int)kind, s));
     return RDCT_OK;

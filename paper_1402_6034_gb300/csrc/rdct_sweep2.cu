@@ -13,10 +13,11 @@ cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchu
     a.jobs = jobs;
     a.chunks = chunks;
     a.nchunks = nchunks;
+    // a programmatic dependent of the table builder: its launch overlaps the builder's tail
     if (kind == RDCT_KIND_RDCT)
-        return launch_staged(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, false, s, a,
+        return launch_staged(sweep2_kernel<RDCT_KIND_RDCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, true, s, a,
                              out, DctConsts{});
-    return launch_staged(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, false, s, a, out,
+    return launch_staged(sweep2_kernel<RDCT_KIND_DCT>, nchunks, 0, 4, kFused2MaxCtas, kFused2Smem, true, s, a, out,
                          make_dct_consts());
 }
 
@@ -40,10 +41,15 @@ struct PlaneBatch {
 
 // One warp per plane: every lane reads the same descriptor (a broadcast from
 // the parameter bank), lane 0 writes the job, and the lanes write the plane's
-// chunks (runs of at most kSweepChunkStrips items of 32 column pairs).
-__global__ void __launch_bounds__(32) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks) {
+// chunks (runs of at most kSweepChunkStrips items of 32 column pairs) and
+// clear its 64 output bins.
+__global__ void __launch_bounds__(32) build_sweep_tables_kernel(const PlaneBatch b, JobDesc *jobs, Chunk *chunks,
+                                                                double *out) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int i = blockIdx.x;
     const int lane = threadIdx.x;
+    out[(int64_t)(b.first + i) * 64 + lane] = 0.0;
+    out[(int64_t)(b.first + i) * 64 + 32 + lane] = 0.0;
     const rdct_plane pl = b.p[i];
     JobDesc j{};
     j.src = pl.ptr;
@@ -72,7 +78,8 @@ int64_t sweep_chunk_count(const rdct_plane &p) {
     return (items + kSweepChunkStrips - 1) / kSweepChunkStrips;
 }
 
-cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, cudaStream_t s) {
+cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, double *out,
+                               cudaStream_t s) {
     int32_t base = 0;
     for (int32_t first = 0; first < n; first += kSweepBuildBatch) {
         PlaneBatch b;
@@ -83,7 +90,7 @@ cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *job
             b.cbase[i] = base;
             base += (int32_t)sweep_chunk_count(planes[first + i]);
         }
-        build_sweep_tables_kernel<<<b.n, 32, 0, s>>>(b, jobs, chunks);
+        build_sweep_tables_kernel<<<b.n, 32, 0, s>>>(b, jobs, chunks, out);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -215,6 +215,9 @@ __global__ void __launch_bounds__(128, KIND == RDCT_KIND_RDCT ? 4 : 3) sweep2_ke
     Fused2Args a = args;
     const int gw = (int)((int64_t)warp * args.nchunks / nwarps);
     a.nchunks = (int)((int64_t)(warp + 1) * args.nchunks / nwarps);
+    // launched as a programmatic dependent of the table builder (which also clears the bins)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     unsigned ub[64];
     float fb[64];
 #pragma unroll
