@@ -214,11 +214,11 @@ class VideoWorkload:
         mse = self.sse.cpu().numpy() / (self.samples / self.frames)
         return {"mean_psnr_db": float(np.mean(10 * np.log10(255.0 ** 2 / mse)))}
 
-    def host_jobs(self):
-        """Pinned host copies of the inputs and outputs for the end-to-end path."""
+    def host_jobs(self, pinned: bool = True):
+        """Host copies (pinned, or plain pageable memory) of the inputs and outputs for the end-to-end path."""
         from paper_1402_6034_gb300.rdct import HostJob
-        hin = [torch.empty(p.shape, dtype=torch.uint8, pin_memory=True) for p in self.planes]
-        hout = [torch.empty(p.shape, dtype=torch.uint8, pin_memory=True) for p in self.planes]
+        hin = [torch.empty(p.shape, dtype=torch.uint8, pin_memory=pinned) for p in self.planes]
+        hout = [torch.empty(p.shape, dtype=torch.uint8, pin_memory=pinned) for p in self.planes]
         for h, p in zip(hin, self.planes):
             h.copy_(p)
         arr = (HostJob * (3 * self.frames))()
@@ -257,10 +257,10 @@ class Batch512Workload(VideoWorkload):
         self.name = self.config["workload"]
         self.kernels_per_step = 2
 
-    def host_jobs(self):
+    def host_jobs(self, pinned: bool = True):
         from paper_1402_6034_gb300.rdct import HostJob
-        hin = [torch.empty(self.planes[0].shape, dtype=torch.uint8, pin_memory=True)]
-        hout = [torch.empty(self.planes[0].shape, dtype=torch.uint8, pin_memory=True)]
+        hin = [torch.empty(self.planes[0].shape, dtype=torch.uint8, pin_memory=pinned)]
+        hout = [torch.empty(self.planes[0].shape, dtype=torch.uint8, pin_memory=pinned)]
         hin[0].copy_(self.planes[0])
         arr = (HostJob * self.frames)()
         for i in range(self.frames):
@@ -792,23 +792,32 @@ def main():
         bufs, arr = wl.host_jobs()
         lib = rdct.load()
 
-        def time_pipeline(mode):
+        def time_pipeline(mode, jobs_arr, budget=6 << 30, depth=3):
+            """Mean seconds per step over e2e_steps after one untimed run (which, for outputs the host never
+            touched, also faults their pages in: its time is returned too)."""
             pipe = ctypes.c_void_p()
-            rdct._check(lib.rdct_pipeline_create(ctypes.c_int64(6 << 30), 3, ctypes.byref(pipe)),
+            rdct._check(lib.rdct_pipeline_create(ctypes.c_int64(budget), depth, ctypes.byref(pipe)),
                         "rdct_pipeline_create")
             rdct._check(lib.rdct_pipeline_set_mode(pipe, mode), "rdct_pipeline_set_mode")
             sse_h = (ctypes.c_double * wl.nimages)()
-            rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h, None),
+            t = time.perf_counter()
+            rdct._check(lib.rdct_pipeline_run(pipe, jobs_arr, len(jobs_arr), wl.nimages, sse_h, None),
                         "rdct_pipeline_run")  # warm
+            first = time.perf_counter() - t
             t = time.perf_counter()
             for _ in range(args.e2e_steps):
-                rdct._check(lib.rdct_pipeline_run(pipe, arr, len(arr), wl.nimages, sse_h, None), "rdct_pipeline_run")
+                rdct._check(lib.rdct_pipeline_run(pipe, jobs_arr, len(jobs_arr), wl.nimages, sse_h, None),
+                            "rdct_pipeline_run")
             dt = (time.perf_counter() - t) / args.e2e_steps
             lib.rdct_pipeline_destroy(pipe)
-            return dt, bool(np.allclose(np.array(sse_h[:]), wl.sse.cpu().numpy(), rtol=0, atol=0))
+            return dt, bool(np.allclose(np.array(sse_h[:]), wl.sse.cpu().numpy(), rtol=0, atol=0)), first
 
-        dt, ok = time_pipeline(rdct.Pipeline.AUTO)
-        dt_s, ok_s = time_pipeline(rdct.Pipeline.STAGED)
+        dt, ok, _ = time_pipeline(rdct.Pipeline.AUTO, arr)
+        dt_s, ok_s, _ = time_pipeline(rdct.Pipeline.STAGED, arr, 2 << 30, 4)
+        del bufs
+        pg_bufs, arr_pg = wl.host_jobs(pinned=False)
+        dt_p, ok_p, first_p = time_pipeline(rdct.Pipeline.AUTO, arr_pg)
+        del pg_bufs
         link = host_link_rate(dev)
         line["e2e"] = {"value": world * wl.samples / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": wl.samples,
                        "d2h_bytes_per_step": wl.samples + 8 * wl.nimages, "ms_per_step": 1000 * dt,
@@ -817,9 +826,15 @@ def main():
                        "sse_matches_device_path": ok,
                        "host_link_GBs_each_way": link,
                        "staged": {"value": world * wl.samples / dt_s / 1e9, "ms_per_step": 1000 * dt_s,
-                                  "api": "rdct_pipeline_run, staged mode: copies into device slots overlapped "
-                                         "with kernels on three streams", "sse_matches_device_path": ok_s}}
-        del bufs
+                                  "api": "rdct_pipeline_run, staged mode (pinned planes, 4 slots of 256 MiB each "
+                                         "way): copies into device slots overlapped with kernels on three streams",
+                                  "sse_matches_device_path": ok_s},
+                       "pageable": {"value": world * wl.samples / dt_p / 1e9, "ms_per_step": 1000 * dt_p,
+                                    "first_run_ms": 1000 * first_p,
+                                    "api": "rdct_pipeline_run (AUTO) on plain pageable host planes: direct mode, "
+                                           "the kernels reach the pages through the host page tables on this "
+                                           "device; the first run also faults in the fresh output pages",
+                                    "sse_matches_device_path": ok_p}}
 
     if rank == 0 and args.workload == "video" and not args.no_extra:
         k = min(args.steps, 20)

@@ -335,14 +335,21 @@ RDCT_API rdct_status rdct_pipeline_run(rdct_pipeline *pipe, const rdct_host_job 
 RDCT_API rdct_status rdct_pipeline_destroy(rdct_pipeline *pipe);
 
 /* How rdct_pipeline_run moves the planes:
- *   AUTO (default)  DIRECT when every plane (src and dst) is pinned host
- *                   memory the device addresses with the same pointer, else
+ *   AUTO (default)  DIRECT when every plane (src and dst) is host memory the
+ *                   device addresses with the same pointer: pinned memory, or
+ *                   plain pageable memory on a device that reaches it through
+ *                   the host's page tables (cudaDevAttrPageableMemoryAccess and
+ *                   ...UsesHostPageTables, as on Grace-Blackwell nodes); else
  *                   STAGED;
  *   STAGED          host->device copies into device slots, kernels on the
  *                   slots, device->host copies, overlapped on three streams;
  *   DIRECT          the fused kernels read and write the host planes over the
  *                   host link (no staging); RDCT_ERR_ARG if a plane is not
- *                   pinned. */
+ *                   such memory.
+ * With pageable planes in DIRECT mode, the first device write to an output
+ * page that the host has never touched faults the page in and is slow; output
+ * buffers reused across runs (or touched once by the host) run at the link
+ * rate. */
 enum { RDCT_PIPELINE_AUTO = 0, RDCT_PIPELINE_STAGED = 1, RDCT_PIPELINE_DIRECT = 2 };
 RDCT_API rdct_status rdct_pipeline_set_mode(rdct_pipeline *pipe, int32_t mode);
 

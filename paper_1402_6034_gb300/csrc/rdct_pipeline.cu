@@ -1,9 +1,11 @@
 // rdct_pipeline.cu -- planes that live in host memory, streamed through the
 // fused path with copies and kernels overlapped.
 //
-// Direct mode (pinned host planes): the fused kernels load and store the
-// planes in host memory themselves, over the host link, and nothing is
-// staged.  Staged mode (any host memory):
+// Direct mode: the fused kernels load and store the planes in host memory
+// themselves, over the host link, and nothing is staged.  It takes pinned
+// planes, and also plain (pageable) host memory on a device that reaches it
+// through the host's page tables (address translation over a coherent
+// host-device link, as on Grace-Blackwell nodes).  Staged mode (any host memory):
 // planes are cut into horizontal bands (whole block rows; 8x8 blocks are
 // independent, Sec. 3), bands are packed into groups that fit one staging
 // slot, and each group goes host->device on one stream, through one batch
@@ -47,6 +49,7 @@ constexpr int kItemsPerChunk = 8;
 struct rdct_pipeline {
     int device = 0;
     int mode = RDCT_PIPELINE_AUTO;
+    bool pageable_direct = false;  // the device addresses pageable host memory through the host page tables
     int64_t slot_bytes = 0;  // per direction
     std::vector<Slot> slots;
     cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
@@ -104,10 +107,12 @@ static rdct_status ensure_tables(Slot &s, int32_t njobs, int32_t nchunks) {
 }
 
 // True when the device can address [p, p + bytes) with the same pointer:
-// pinned (page-locked) host memory under unified addressing.  The first and
-// the last byte are checked; a plane is one user buffer, so both ends being
-// pinned means the buffer was pinned as a whole.
-static bool device_addressable(const void *p, int64_t bytes) {
+// pinned (page-locked) host memory under unified addressing, or, when
+// pageable_ok (the device reads and writes pageable memory through the host
+// page tables), plain host memory that CUDA does not know.  The first and the
+// last byte are checked; a plane is one user buffer, so both ends of one kind
+// mean the buffer is of that kind as a whole.
+static bool device_addressable(const void *p, int64_t bytes, bool pageable_ok) {
     const void *ends[2] = {p, static_cast<const uint8_t *>(p) + (bytes > 0 ? bytes - 1 : 0)};
     for (const void *q : ends) {
         cudaPointerAttributes a;
@@ -115,7 +120,9 @@ static bool device_addressable(const void *p, int64_t bytes) {
             cudaGetLastError();
             return false;
         }
-        if (a.type != cudaMemoryTypeHost || a.devicePointer != q) return false;
+        const bool pinned = a.type == cudaMemoryTypeHost && a.devicePointer == q;
+        const bool pageable = pageable_ok && a.type == cudaMemoryTypeUnregistered;
+        if (!pinned && !pageable) return false;
     }
     return true;
 }
@@ -198,6 +205,12 @@ rdct_status rdct_pipeline_create(int64_t device_budget_bytes, int32_t depth, rdc
     rdct_pipeline *p = new (std::nothrow) rdct_pipeline();
     if (!p) return set_error(RDCT_ERR_OOM, "rdct_pipeline_create: host allocation failed");
     cudaGetDevice(&p->device);
+    {
+        int pma = 0, host_tables = 0;
+        cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, p->device);
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, p->device);
+        p->pageable_direct = pma == 1 && host_tables == 1;
+    }
     p->slot_bytes = (device_budget_bytes / depth / 2) & ~(int64_t)255;
     p->slots.resize(depth);
     cudaError_t e = cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking);
@@ -250,10 +263,14 @@ rdct_status rdct_pipeline_run(rdct_pipeline *p, const rdct_host_job *jobs, int32
     for (int32_t i = 0; i < njobs && direct; ++i) {
         const rdct_host_job &j = jobs[i];
         const int64_t bytes = (int64_t)(j.h - 1) * j.pitch + j.w;
-        direct = device_addressable(j.src, bytes) && (!j.dst || device_addressable(j.dst, bytes));
+        direct = device_addressable(j.src, bytes, p->pageable_direct) &&
+                 (!j.dst || device_addressable(j.dst, bytes, p->pageable_direct));
     }
     if (p->mode == RDCT_PIPELINE_DIRECT && !direct)
-        return set_error(RDCT_ERR_ARG, "rdct_pipeline_run: direct mode needs pinned host planes");
+        return set_error(RDCT_ERR_ARG, p->pageable_direct
+                                           ? "rdct_pipeline_run: direct mode needs host planes (pinned or pageable)"
+                                           : "rdct_pipeline_run: direct mode needs pinned host planes (this device "
+                                             "does not address pageable memory)");
     if (direct) {
         rdct_status st = run_direct(p, jobs, njobs, acc8);
         if (st) return st;

@@ -67,3 +67,27 @@ def block_norms(img: np.ndarray) -> np.ndarray:
     h, w = img.shape
     b = img.astype(np.float64).reshape(h // 8, 8, w // 8, 8).transpose(0, 2, 1, 3).reshape(-1, 64)
     return np.sqrt((b ** 2).sum(axis=1))
+
+
+def pageable_direct_supported() -> bool:
+    """Whether the current device reads and writes pageable host memory through the host's page tables
+    (cudaDevAttrPageableMemoryAccess = 88 and cudaDevAttrPageableMemoryAccessUsesHostPageTables = 100, asked
+    of the CUDA runtime directly)."""
+    import ctypes
+    import glob
+    import os
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        for c in sorted(glob.glob(os.path.join(d, "lib64", "libcudart.so*"))) if d else []:
+            try:
+                rt = ctypes.CDLL(c)
+            except OSError:
+                continue
+            dev, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            if rt.cudaGetDevice(ctypes.byref(dev)) != 0:
+                return False
+            if rt.cudaDeviceGetAttribute(ctypes.byref(a), 88, dev) != 0:
+                return False
+            if rt.cudaDeviceGetAttribute(ctypes.byref(b), 100, dev) != 0:
+                return False
+            return a.value == 1 and b.value == 1
+    return False

@@ -1,6 +1,6 @@
 """The host pipeline (rdct_pipeline_run): planes in host memory, staged through device slots
-(copies overlapped with kernels) or read and written in place by the kernels (direct mode,
-pinned memory).  Both must give exactly what the device-resident path gives: the same uint8
+(copies overlapped with kernels) or read and written in place by the kernels (direct mode:
+pinned memory, and pageable memory on a device that reaches it through the host page tables).  Both must give exactly what the device-resident path gives: the same uint8
 reconstruction and the same per-image error (576 * SSE is an exact integer on every route);
 a few planes are also checked against the oracle."""
 import numpy as np
@@ -9,7 +9,7 @@ import torch
 
 from oracle import oracle as orc
 from paper_1402_6034_gb300 import rdct, synth
-from tests.gpu_helpers import assert_u8_close, cuda_or_skip
+from tests.gpu_helpers import assert_u8_close, cuda_or_skip, pageable_direct_supported
 
 pytestmark = pytest.mark.gpu
 
@@ -96,12 +96,38 @@ def test_pipeline_u8_error(dev, mode):
     np.testing.assert_allclose(sse, _device_reference(jobs, dev)[1], rtol=1e-12, atol=1e-9)
 
 
-def test_pipeline_sse_only_and_direct_refuses_pageable(dev):
+def test_pipeline_sse_only_and_direct_on_pageable(dev):
+    """Direct mode on pageable planes: refused where the device cannot address pageable memory, and
+    otherwise exactly the device path's result."""
     jobs = [(src, None, r, img) for src, _, r, img in _planes(3, True)]
     ref = _device_reference(jobs, dev)[1]
     p = rdct.Pipeline(device_budget_bytes=32 << 20, depth=2, mode=rdct.Pipeline.DIRECT)
     np.testing.assert_allclose(p.run(jobs, 4), ref, rtol=1e-12, atol=1e-9)
     pageable = [(torch.from_numpy(src.numpy().copy()), None, r, img) for src, _, r, img in jobs]
-    with pytest.raises(rdct.RdctError):
-        p.run(pageable, 4)
+    if pageable_direct_supported():
+        np.testing.assert_allclose(p.run(pageable, 4), ref, rtol=1e-12, atol=1e-9)
+    else:
+        with pytest.raises(rdct.RdctError):
+            p.run(pageable, 4)
     p.close()
+
+
+@pytest.mark.parametrize("touched", [True, False])
+def test_pipeline_direct_pageable_output(dev, touched):
+    """Pageable planes in and out through the kernels (direct mode where the device supports it), with
+    output buffers the host has or has not touched: the same bytes and errors as the device path."""
+    if not pageable_direct_supported():
+        pytest.skip("the device does not address pageable host memory")
+    jobs = []
+    for src, _, r, img in _planes(5, False):
+        h, w = src.shape
+        pitch = src.stride(0)  # one pitch for source and destination
+        dst = np.full((h, pitch), 7, np.uint8) if touched else np.empty((h, pitch), np.uint8)
+        jobs.append((src, torch.from_numpy(dst)[:, :w], r, img))
+    ref_out, ref_sse = _device_reference(jobs, dev)
+    p = rdct.Pipeline(device_budget_bytes=32 << 20, depth=2, mode=rdct.Pipeline.DIRECT)
+    sse = p.run(jobs, 4)
+    p.close()
+    for (src, dst, r, img), ref in zip(jobs, ref_out):
+        assert torch.equal(dst, ref), (src.shape, r)
+    np.testing.assert_allclose(sse, ref_sse, rtol=1e-12, atol=1e-9)
