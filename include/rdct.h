@@ -363,9 +363,13 @@ typedef struct {
     int32_t max_wait_us;         /* how long a lone request may wait for company */
 } rdct_server_opts;
 
-/* A request: an image of `planes` planes (1..4), all w x h, in host memory:
- * plane p starts at src + p * plane_stride (plane_stride 0 means pitch * h),
- * rows are `pitch` bytes apart; dst uses the same layout. */
+/* A request: an image of `planes` planes (1..4), all w x h, in host memory
+ * (pinned or pageable): plane p starts at src + p * plane_stride
+ * (plane_stride 0 means pitch * h), rows are `pitch` bytes apart; dst uses the
+ * same layout.  Pinned planes move on the copy engines; pageable planes, on a
+ * device that reaches pageable memory through the host page tables, are moved
+ * by copy kernels (asynchronous, at the host-link rate), else by the driver's
+ * staged copies. */
 typedef struct {
     const uint8_t *src; /* host */
     uint8_t *dst;       /* host, receives the uint8 reconstruction (same layout), may be NULL */

@@ -175,5 +175,15 @@ cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *job
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
                          int32_t nplanes, cudaStream_t s);
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s);
+// 2-D copy of w bytes by h rows done by a kernel (for pageable host memory the
+// device addresses through the host page tables).
+cudaError_t launch_copy2d(void *dst, int64_t dpitch, const void *src, int64_t spitch, int32_t w, int32_t h,
+                          cudaStream_t s);
+// True when the current device reads and writes pageable host memory through
+// the host's page tables.
+bool device_pageable_access(int device);
+// True when every byte of [p, p + bytes) is plain (pageable) host memory that
+// CUDA does not know (first and last byte checked).
+bool is_pageable_host(const void *p, int64_t bytes);
 
 }  // namespace rdct

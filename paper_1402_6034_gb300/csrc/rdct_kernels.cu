@@ -434,6 +434,68 @@ cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s, void
     return cudaGetLastError();
 }
 
+// 2-D byte copy by the SMs, for host memory that the device reaches through
+// the host page tables (pageable memory), where the copy engines would need
+// the driver's staging: rows strided over grid.y, each row's elements of VEC
+// bytes strided over the threads of grid.x.
+template <int VEC>
+__global__ void copy2d_kernel(uint8_t *dst, int64_t dpitch, const uint8_t *src, int64_t spitch, int32_t w, int32_t h) {
+    const int32_t per_row = w / VEC;
+    for (int32_t y = blockIdx.y; y < h; y += gridDim.y) {
+        const uint8_t *s = src + (int64_t)y * spitch;
+        uint8_t *d = dst + (int64_t)y * dpitch;
+        for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < per_row; x += gridDim.x * blockDim.x) {
+            if constexpr (VEC == 16) reinterpret_cast<uint4 *>(d)[x] = reinterpret_cast<const uint4 *>(s)[x];
+            else if constexpr (VEC == 8) reinterpret_cast<uint2 *>(d)[x] = reinterpret_cast<const uint2 *>(s)[x];
+            else d[x] = s[x];
+        }
+    }
+}
+
+bool device_pageable_access(int device) {
+    int pma = 0, host_tables = 0;
+    if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return pma == 1 && host_tables == 1;
+}
+
+bool is_pageable_host(const void *p, int64_t bytes) {
+    const void *ends[2] = {p, static_cast<const uint8_t *>(p) + (bytes > 0 ? bytes - 1 : 0)};
+    for (const void *q : ends) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeUnregistered) return false;
+    }
+    return true;
+}
+
+cudaError_t launch_copy2d(void *dst, int64_t dpitch, const void *src, int64_t spitch, int32_t w, int32_t h,
+                          cudaStream_t s) {
+    if (w <= 0 || h <= 0) return cudaSuccess;
+    auto aligned = [&](int a) {
+        return reinterpret_cast<uintptr_t>(dst) % a == 0 && reinterpret_cast<uintptr_t>(src) % a == 0 &&
+               dpitch % a == 0 && spitch % a == 0 && w % a == 0;
+    };
+    const int vec = aligned(16) ? 16 : aligned(8) ? 8 : 1;
+    const int32_t per_row = w / vec;
+    const int tx = per_row >= 256 ? 256 : ((per_row + 31) / 32) * 32;
+    const int gx = (per_row + tx * 4 - 1) / (tx * 4);
+    const int gy = h < 4096 ? h : 4096;
+    const dim3 grid((unsigned)(gx < 1 ? 1 : gx), (unsigned)gy);
+    auto *d = static_cast<uint8_t *>(dst);
+    auto *sp = static_cast<const uint8_t *>(src);
+    if (vec == 16) copy2d_kernel<16><<<grid, tx, 0, s>>>(d, dpitch, sp, spitch, w, h);
+    else if (vec == 8) copy2d_kernel<8><<<grid, tx, 0, s>>>(d, dpitch, sp, spitch, w, h);
+    else copy2d_kernel<1><<<grid, tx, 0, s>>>(d, dpitch, sp, spitch, w, h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
                          int32_t nplanes, cudaStream_t s) {
     (void)nplanes;

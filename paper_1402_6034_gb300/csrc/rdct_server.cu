@@ -57,6 +57,7 @@ struct Req {
     int64_t arena_off = -1;
     Clock::time_point t_submit, t_admit;
     cudaEvent_t copied = nullptr;
+    bool src_pageable = false, dst_pageable = false;  // moved by copy kernels (see rdct_server.pageable)
     bool admitted = false;
     rdct_result res{};
     bool done = false;
@@ -82,6 +83,11 @@ struct rdct_server {
     rdct_arena *arena = nullptr;
     cudaStream_t copy = nullptr;
     std::vector<Lane> lanes;
+    // the device reads and writes pageable host memory through the host page
+    // tables: request planes in such memory are moved by copy kernels, which
+    // stay asynchronous, instead of the copy engines (whose pageable copies
+    // the driver stages, synchronously)
+    bool pageable = false;
 
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -208,9 +214,14 @@ rdct_status launch_batch(rdct_server *S, Lane &L) {
         if (!r.q.dst) continue;
         const int64_t plane = (int64_t)r.q.w * r.q.h;
         uint8_t *out = S->d_pool + r.arena_off + r.q.planes * plane;
-        for (int p = 0; p < r.q.planes; ++p)
-            RDCT_CUDA_TRY(cudaMemcpy2DAsync(r.q.dst + p * r.q.plane_stride, r.q.pitch, out + p * plane,
-                                            r.q.w, r.q.w, r.q.h, cudaMemcpyDeviceToHost, L.s));
+        for (int p = 0; p < r.q.planes; ++p) {
+            if (r.dst_pageable)
+                RDCT_CUDA_TRY(launch_copy2d(r.q.dst + p * r.q.plane_stride, r.q.pitch, out + p * plane, r.q.w, r.q.w,
+                                            r.q.h, L.s));
+            else
+                RDCT_CUDA_TRY(cudaMemcpy2DAsync(r.q.dst + p * r.q.plane_stride, r.q.pitch, out + p * plane,
+                                                r.q.w, r.q.w, r.q.h, cudaMemcpyDeviceToHost, L.s));
+        }
     }
     RDCT_CUDA_TRY(cudaMemcpyAsync(L.h_acc, L.d_acc, 2 * n * sizeof(unsigned long long), cudaMemcpyDeviceToHost, L.s));
     RDCT_CUDA_TRY(cudaEventRecord(L.done, L.s));
@@ -284,9 +295,14 @@ void scheduler(rdct_server *S) {
             S->peak_resident = std::max(S->peak_resident, rdct_arena_used(S->arena));
             const int64_t plane = (int64_t)r->q.w * r->q.h;
             cudaEventCreateWithFlags(&r->copied, cudaEventDisableTiming);
-            for (int p = 0; p < r->q.planes; ++p)
-                cudaMemcpy2DAsync(S->d_pool + off + p * plane, r->q.w, r->q.src + p * r->q.plane_stride,
-                                  r->q.pitch, r->q.w, r->q.h, cudaMemcpyHostToDevice, S->copy);
+            for (int p = 0; p < r->q.planes; ++p) {
+                if (r->src_pageable)
+                    launch_copy2d(S->d_pool + off + p * plane, r->q.w, r->q.src + p * r->q.plane_stride, r->q.pitch,
+                                  r->q.w, r->q.h, S->copy);
+                else
+                    cudaMemcpy2DAsync(S->d_pool + off + p * plane, r->q.w, r->q.src + p * r->q.plane_stride,
+                                      r->q.pitch, r->q.w, r->q.h, cudaMemcpyHostToDevice, S->copy);
+            }
             cudaEventRecord(r->copied, S->copy);
             S->ready.push_back(r);
         }
@@ -377,6 +393,7 @@ rdct_status rdct_server_create(const rdct_server_opts *opts, rdct_server **serve
     if (!S) return set_error(RDCT_ERR_OOM, "rdct_server_create: host allocation failed");
     S->opts = *opts;
     cudaGetDevice(&S->device);
+    S->pageable = device_pageable_access(S->device);
     if (cudaMalloc(&S->d_pool, opts->device_budget_bytes) != cudaSuccess) {
         server_free(S);
         return set_error(RDCT_ERR_OOM, "rdct_server_create: device budget allocation failed");
@@ -412,6 +429,11 @@ rdct_status rdct_server_submit(rdct_server *S, const rdct_request *req, uint64_t
     if (r->q.plane_stride == 0) r->q.plane_stride = r->q.pitch * r->q.h;
     request_bytes(*req, &r->bytes);
     r->bytes = (r->bytes + 255) & ~(int64_t)255;
+    if (S->pageable) {
+        const int64_t extent = (int64_t)(r->q.planes - 1) * r->q.plane_stride + (int64_t)(r->q.h - 1) * r->q.pitch + r->q.w;
+        r->src_pageable = is_pageable_host(r->q.src, extent);
+        r->dst_pageable = r->q.dst && is_pageable_host(r->q.dst, extent);
+    }
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return set_error(RDCT_ERR_BUSY, "rdct_server_submit: server is shutting down");
     if (r->bytes > S->opts.device_budget_bytes) {

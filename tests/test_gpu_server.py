@@ -73,6 +73,32 @@ def test_results_match_oracle(dev):
     srv.close()
 
 
+def test_pageable_requests_equal_pinned(dev):
+    """Requests whose planes live in plain pageable memory (moved by copy kernels where the device reaches
+    such memory through the host page tables, else by the driver's copies), with padded pitches and a
+    plane stride: results and images identical to the same requests in pinned memory."""
+    reqs = _requests(8, seed=5)
+    srv = rdct.Server(device_budget_bytes=256 << 20, max_batch=4, streams=2)
+    ref_outs, ref_res = _run(srv, reqs)
+    pageable, outs, tickets = [], [], []
+    for src, r in reqs:
+        p, h, w = src.shape
+        buf = np.full((p, h + 2, w + 40), 5, np.uint8)  # padded rows and a gap between planes
+        buf[:, :h, :w] = src.numpy()
+        view = torch.from_numpy(buf)[:, :h, :w]
+        out_buf = torch.from_numpy(np.full((p, h + 2, w + 40), 9, np.uint8))
+        pageable.append((view, r))
+        outs.append(out_buf)
+        tickets.append(srv.submit(view, r, out_buf[:, :h, :w]))
+    res = [srv.wait(t) for t in tickets]
+    for (view, r), out_buf, ref_out, rr, ref in zip(pageable, outs, ref_outs, res, ref_res):
+        p, h, w = view.shape
+        assert torch.equal(out_buf[:, :h, :w], ref_out)
+        assert bool((out_buf[:, h:, :] == 9).all()) and bool((out_buf[:, :, w:] == 9).all())
+        assert rr["sse"] == ref["sse"] and rr["sse_u8"] == ref["sse_u8"]
+    srv.close()
+
+
 def test_alone_equals_mixed(dev):
     reqs = _requests(16, seed=2)
     alone = []
