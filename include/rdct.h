@@ -63,7 +63,7 @@ typedef enum {
     RDCT_ERR_CUDA = 5,       /* a CUDA runtime call or kernel failed */
     RDCT_ERR_TIMEOUT = 6,    /* a wait ran out before the work completed */
     RDCT_ERR_BUSY = 7,       /* queue full; retry later */
-    RDCT_ERR_NOT_FOUND = 8,  /* unknown ticket or handle */
+    RDCT_ERR_NOT_FOUND = 8,  /* unknown ticket or handle, unreadable file */
     RDCT_ERR_CANCELLED = 9   /* the request was cancelled before it ran */
 } rdct_status;
 
@@ -306,6 +306,22 @@ RDCT_API rdct_status rdct_batch_plan_destroy(rdct_plan *plan);
  * again, and dropped if it stays that noisy.  The default shape is kept
  * unless a candidate's median beats it by more than 1%. */
 RDCT_API rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, rdct_tune *best, rdct_stream stream);
+/* The autotune cache across processes.  Its keys name the GPU model (device
+ * name, compute capability, SM count) and the batch's shape class, so a saved
+ * cache applies to any device of that model.
+ * rdct_autotune_cache_save writes every entry of this process's cache to
+ * `path` (overwritten), one JSON object per line:
+ *   {"key": "...", "warps_per_cta": 4, "ctas_per_sm": 4, "items_per_chunk": 32,
+ *    "blocks_per_thread": 2, "staging": 0}
+ * rdct_autotune_cache_load merges the lines of that exact form from `path`
+ * into the cache (lines in any other form, or with an invalid launch shape,
+ * are skipped) and reports how many it took in *loaded (may be NULL); plans
+ * created with tune NULL then use them.  rdct_autotune_cache_clear empties the
+ * cache.  Errors: RDCT_ERR_ARG (null path, unwritable file), RDCT_ERR_NOT_FOUND
+ * (unreadable file). */
+RDCT_API rdct_status rdct_autotune_cache_save(const char *path);
+RDCT_API rdct_status rdct_autotune_cache_load(const char *path, int32_t *loaded);
+RDCT_API rdct_status rdct_autotune_cache_clear(void);
 
 /* -------------------------------------------- host-resident streaming path */
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -183,6 +184,23 @@ rdct_status check_sse_args(const char *what, double *sse, double *sse8) {
 std::mutex g_tune_mu;
 std::map<std::string, rdct_tune> g_tune_cache;
 
+// The GPU model a tune was measured on (name, compute capability, SM count;
+// not the device index), so that a saved cache applies to any device of that
+// model.  Characters that would need escaping in the cache file are replaced.
+std::string gpu_identity() {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "nodev";
+    }
+    std::string name = prop.name;
+    for (char &c : name)
+        if (c == '"' || c == '\\' || c == ':' || (unsigned char)c < 32) c = '_';
+    return name + "/sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "/" +
+           std::to_string(prop.multiProcessorCount);
+}
+
 std::string shape_key(const rdct_job *jobs, int32_t njobs) {
     // shape class: job count, total blocks (log2 bucket) and blocks per r class
     int64_t blocks = 0;
@@ -193,9 +211,7 @@ std::string shape_key(const rdct_job *jobs, int32_t njobs) {
         const int d = diag_class_host(jobs[i].r);
         per_class[d <= 5 ? 0 : (d <= 8 ? 1 : 2)] += b;
     }
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::string k = "dev" + std::to_string(dev) + ":n" + std::to_string(njobs);
+    std::string k = gpu_identity() + ":n" + std::to_string(njobs);
     int lg = 0;
     while ((int64_t)1 << (lg + 1) <= blocks) ++lg;
     k += ":b" + std::to_string(lg);
@@ -417,6 +433,59 @@ rdct_status rdct_autotune(const rdct_job *jobs, int32_t njobs, int32_t nimages, 
     *best = best_t;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[shape_key(jobs, njobs)] = best_t;
+    return RDCT_OK;
+}
+
+rdct_status rdct_autotune_cache_save(const char *path) {
+    if (!path) return set_error(RDCT_ERR_ARG, "rdct_autotune_cache_save: null path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE *f = std::fopen(path, "w");
+    if (!f) return set_error(RDCT_ERR_ARG, std::string("rdct_autotune_cache_save: cannot write ") + path);
+    for (const auto &kv : g_tune_cache) {
+        const rdct_tune &t = kv.second;
+        std::fprintf(f,
+                     "{\"key\": \"%s\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"items_per_chunk\": %d, "
+                     "\"blocks_per_thread\": %d, \"staging\": %d}\n",
+                     kv.first.c_str(), t.warps_per_cta, t.ctas_per_sm, t.items_per_chunk, t.blocks_per_thread,
+                     t.staging);
+    }
+    const bool ok = std::fflush(f) == 0;
+    std::fclose(f);
+    if (!ok) return set_error(RDCT_ERR_ARG, std::string("rdct_autotune_cache_save: write failed: ") + path);
+    return RDCT_OK;
+}
+
+rdct_status rdct_autotune_cache_load(const char *path, int32_t *loaded) {
+    if (!path) return set_error(RDCT_ERR_ARG, "rdct_autotune_cache_load: null path");
+    FILE *f = std::fopen(path, "r");
+    if (!f) return set_error(RDCT_ERR_NOT_FOUND, std::string("rdct_autotune_cache_load: cannot read ") + path);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int32_t n = 0;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        char key[512];
+        rdct_tune t{};
+        int used = 0;
+        // only the exact form rdct_autotune_cache_save writes; anything else is skipped
+        if (std::sscanf(line,
+                        "{\"key\": \"%511[^\"]\", \"warps_per_cta\": %d, \"ctas_per_sm\": %d, \"items_per_chunk\": "
+                        "%d, \"blocks_per_thread\": %d, \"staging\": %d}%n",
+                        key, &t.warps_per_cta, &t.ctas_per_sm, &t.items_per_chunk, &t.blocks_per_thread, &t.staging,
+                        &used) != 6 ||
+            used == 0)
+            continue;
+        if (validate_tune(t) != RDCT_OK) continue;
+        g_tune_cache[key] = t;
+        ++n;
+    }
+    std::fclose(f);
+    if (loaded) *loaded = n;
+    return RDCT_OK;
+}
+
+rdct_status rdct_autotune_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache.clear();
     return RDCT_OK;
 }
 

@@ -118,6 +118,9 @@ _SIGS = {
     "rdct_batch_plan_kernels": [_vp, ctypes.POINTER(_i32)],
     "rdct_batch_plan_destroy": [_vp],
     "rdct_autotune": [ctypes.POINTER(Job), _i32, _i32, ctypes.POINTER(Tune), _vp],
+    "rdct_autotune_cache_save": [ctypes.c_char_p],
+    "rdct_autotune_cache_load": [ctypes.c_char_p, ctypes.POINTER(_i32)],
+    "rdct_autotune_cache_clear": [],
     "rdct_pipeline_create": [_i64, _i32, ctypes.POINTER(_vp)],
     "rdct_pipeline_run": [_vp, ctypes.POINTER(HostJob), _i32, _i32, _vp, _vp],
     "rdct_pipeline_destroy": [_vp],
@@ -447,6 +450,23 @@ def autotune(jobs: list[BatchJob], nimages: int, stream=None) -> dict:
     t = Tune()
     _check(load().rdct_autotune(arr, len(jobs), nimages, ctypes.byref(t), _stream(stream)), "rdct_autotune")
     return t.as_dict()
+
+
+def autotune_cache_save(path: str) -> None:
+    """rdct_autotune_cache_save: this process's autotune results to `path` (one JSON object per line)."""
+    _check(load().rdct_autotune_cache_save(os.fsencode(path)), "rdct_autotune_cache_save")
+
+
+def autotune_cache_load(path: str) -> int:
+    """rdct_autotune_cache_load: merge a saved cache; returns the number of entries taken."""
+    n = _i32()
+    _check(load().rdct_autotune_cache_load(os.fsencode(path), ctypes.byref(n)), "rdct_autotune_cache_load")
+    return n.value
+
+
+def autotune_cache_clear() -> None:
+    """rdct_autotune_cache_clear: forget every autotune result of this process."""
+    _check(load().rdct_autotune_cache_clear(), "rdct_autotune_cache_clear")
 
 
 # ---------------------------------------------------------- host streaming

@@ -225,12 +225,18 @@ def test_batch_equals_per_plane(dev):
         assert torch.equal(a, j.dst)
 
 
-def test_autotune_picks_a_valid_shape(dev):
+def test_autotune_picks_a_valid_shape(dev, tmp_path):
     specs, jobs, host = _batch(dev, n_images=8, seed=11)
     t = rdct.autotune(jobs, len(specs))
     assert 1 <= t["warps_per_cta"] <= 32 and t["items_per_chunk"] >= 1 and t["staging"] in (0, 1)
     plan = rdct.BatchPlan(jobs, len(specs))  # picks the cached tune
     assert plan.tune == t
+    # the cache survives a save, a clear and a load (as another process would see it)
+    path = str(tmp_path / "tune_cache.jsonl")
+    rdct.autotune_cache_save(path)
+    rdct.autotune_cache_clear()
+    assert rdct.autotune_cache_load(path) >= 1
+    assert rdct.BatchPlan(jobs, len(specs)).tune == t
     sse = torch.empty(len(specs), dtype=torch.float64, device=dev)
     plan.run(sse)
     torch.cuda.synchronize()
