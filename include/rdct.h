@@ -269,7 +269,9 @@ typedef struct rdct_plan rdct_plan;
 /* Build a plan over `njobs` planes: every plane is cut into work items
  * (runs of 32 column pairs, a pair being two vertically adjacent 8x8 blocks;
  * for planes that take TMA staging, 32-column segments of a row pair),
- * items are grouped into chunks ordered by r, and the job and chunk tables
+ * items are grouped into chunks ordered by r (with tune NULL and no cached
+ * tune, each r's chunks are made small enough that the warps of its launch
+ * get even shares), and the job and chunk tables
  * (and the planes' tensor maps) are uploaded to the device once.  tune may be
  * NULL (defaults / autotune cache).  All job pointers must stay valid while
  * the plan is used.  Errors: RDCT_ERR_ARG / RDCT_ERR_SHAPE naming the first

@@ -17,9 +17,11 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "rdct_device.cuh"
+#include "rdct_fused2.cuh"
 #include "rdct_internal.h"
 
 using namespace rdct;
@@ -37,6 +39,7 @@ struct rdct_plan {
     JobDesc *d_jobs = nullptr;
     Chunk *d_chunks = nullptr;
     bool tma = false;                // some jobs use the TMA-staged kernel (items: row pair x 32-column segment)
+    bool balance_chunks = false;     // default tune: chunk sizes chosen per r so that the warps get equal shares
     std::vector<unsigned char> maps; // two encoded tensor maps per job (zeros for jobs without TMA)
     std::vector<char> job_tma;       // per job: TMA staging
     unsigned char *d_maps = nullptr;
@@ -106,6 +109,40 @@ rdct_status validate_jobs(const rdct_job *jobs, int32_t njobs, int32_t nimages) 
     return RDCT_OK;
 }
 
+// CTAs per SM of the two-block kernel for r (its launch bounds, at most kFused2MaxCtas).
+template <int... I>
+constexpr int fused2_min_blocks(int r, std::integer_sequence<int, I...>) {
+    int v = kFused2MaxCtas;
+    ((v = (r == I + 1) ? Fused2Shape<I + 1>::min_blocks : v), ...);
+    return v;
+}
+int fused2_ctas_per_sm(int r) {
+    const int m = fused2_min_blocks(r, std::make_integer_sequence<int, 64>{});
+    return m < kFused2MaxCtas ? m : kFused2MaxCtas;
+}
+
+// Items per chunk for one persistent two-block launch of `items` work items
+// over `nwarps` warps, which take chunks c = warp, warp + nwarps, ...: the
+// largest size up to `per` whose rounds leave the warps at least 97 % evenly
+// loaded (the most even one if none does).  A small batch thus gets smaller
+// chunks; a large one keeps `per`.
+int balanced_chunk(int64_t items, int64_t nwarps, int per) {
+    if (items <= 0 || nwarps <= 0) return per;
+    int best = per;
+    double best_eff = 0.0;
+    for (int c = per; c >= 1; --c) {
+        const int64_t chunks = (items + c - 1) / c;
+        const int64_t rounds = (chunks + nwarps - 1) / nwarps;
+        const double eff = (double)items / ((double)nwarps * (double)c * (double)rounds);
+        if (eff >= 0.97) return c;
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = c;
+        }
+    }
+    return best;
+}
+
 void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     const int vrows = p->tune.blocks_per_thread == 2 ? kFusedVRows : 1;
     p->jobs.resize(njobs);
@@ -132,11 +169,29 @@ void build_tables(rdct_plan *p, const rdct_job *jobs, int32_t njobs) {
     }
     std::vector<Chunk> ch;
     const int per = p->tune.items_per_chunk;
+    // chunk size per launch class (one persistent launch per class and staging form)
+    std::vector<int> per_class(2 * kBatchGroups, per);
+    if (p->balance_chunks && p->tune.blocks_per_thread == 2) {
+        std::vector<int64_t> items_of_class(2 * kBatchGroups, 0);
+        for (int32_t i = 0; i < njobs; ++i) {
+            const bool t = p->job_tma[i] != 0;
+            items_of_class[fused_class_of(p->jobs[i].r, 2) + (t ? kBatchGroups : 0)] +=
+                t ? tma_items_of(p->jobs[i]) : strips_of(p->jobs[i], vrows);
+        }
+        for (int c = 0; c < 2 * kBatchGroups; ++c) {
+            if (!items_of_class[c]) continue;
+            const int r = (c % kBatchGroups) + 1;  // two-block classes are r - 1
+            int ctas = fused2_ctas_per_sm(r);
+            if (p->tune.ctas_per_sm > 0 && p->tune.ctas_per_sm < ctas) ctas = p->tune.ctas_per_sm;
+            per_class[c] = balanced_chunk(items_of_class[c], (int64_t)sm_count() * ctas * 4, per);
+        }
+    }
     for (int32_t i = 0; i < njobs; ++i) {
         const bool t = p->job_tma[i] != 0;
         const int items = t ? tma_items_of(p->jobs[i]) : strips_of(p->jobs[i], vrows);
         const int c = fused_class_of(p->jobs[i].r, p->tune.blocks_per_thread) + (t ? kBatchGroups : 0);
-        for (int it = 0; it < items; it += per) ch.push_back(Chunk{i, it, std::min(per, items - it), c});
+        const int pc = per_class[c];
+        for (int it = 0; it < items; it += pc) ch.push_back(Chunk{i, it, std::min(pc, items - it), c});
     }
     std::stable_sort(ch.begin(), ch.end(), [](const Chunk &a, const Chunk &b) { return a.cls < b.cls; });
     p->chunks = std::move(ch);
@@ -230,12 +285,14 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     rdct_status st = validate_jobs(jobs, njobs, nimages);
     if (st) return st;
     rdct_tune t = default_tune();
+    bool balance = false;
     if (tune) {
         t = *tune;
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(shape_key(jobs, njobs));
         if (it != g_tune_cache.end()) t = it->second;
+        else balance = true;
     }
     st = validate_tune(t);
     if (st) return st;
@@ -243,6 +300,7 @@ rdct_status rdct_batch_plan_create(const rdct_job *jobs, int32_t njobs, int32_t 
     if (!p) return set_error(RDCT_ERR_OOM, "rdct_batch_plan_create: host allocation failed");
     p->nimages = nimages;
     p->tune = t;
+    p->balance_chunks = balance;
     cudaGetDevice(&p->device);
     build_tables(p, jobs, njobs);
     const size_t jb = p->jobs.size() * sizeof(JobDesc), cb = p->chunks.size() * sizeof(Chunk);

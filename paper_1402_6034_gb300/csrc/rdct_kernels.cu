@@ -21,6 +21,8 @@ namespace rdct {
 // In place: uint64 576 * SSE -> double SSE (slots not nullptr), and uint64
 // squared errors of 8-bit reconstructions -> double (slots8 not nullptr).
 __global__ void sse576_to_double_kernel(void *slots, void *slots8, int32_t n) {
+    // launched as a programmatic dependent of the kernels that filled the slots
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         if (slots != nullptr) {
@@ -430,8 +432,16 @@ cudaError_t launch_mse_finalize(const unsigned long long *acc_u64, const double 
 
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s, void *slots8) {
     if (n <= 0) return cudaSuccess;
-    sse576_to_double_kernel<<<(n + 255) / 256, 256, 0, s>>>(slots, slots8, n);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((n + 255) / 256));
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sse576_to_double_kernel, slots, slots8, n);
 }
 
 // 2-D byte copy by the SMs, for host memory that the device reaches through
