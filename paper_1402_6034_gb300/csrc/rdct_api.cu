@@ -158,6 +158,11 @@ rdct_status rdct_sync(rdct_stream stream) {
         take_tma_timeouts_r12, take_tma_timeouts_r13, take_tma_timeouts_r14, take_tma_timeouts_r15};
     unsigned int t = 0;
     for (auto take : takers) t += take();
+    const unsigned int ts = take_sweep_tc_timeouts();
+    if (ts)
+        return set_error(RDCT_ERR_TIMEOUT, "rdct_sync: " + std::to_string(ts) +
+                                               " waits of the tensor-core sweep for its MMAs ran out; those groups "
+                                               "stopped early and the sweep results are incomplete");
     if (t)
         return set_error(RDCT_ERR_TIMEOUT, "rdct_sync: " + std::to_string(t) +
                                                " TMA waits for a staged box ran out; the launches that hit them "
@@ -260,13 +265,15 @@ rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, doub
     if (kind != RDCT_KIND_RDCT && kind != RDCT_KIND_DCT) return set_error(RDCT_ERR_ARG, "rdct_sweep: bad kind");
     if (reinterpret_cast<uintptr_t>(sse_by_r) % 8) return set_error(RDCT_ERR_ARG, "rdct_sweep: misaligned output");
     if (n == 0) return RDCT_OK;
-    int64_t nchunks = 0;
+    int64_t nchunks = 0, ntiles = 0;
     for (int32_t i = 0; i < n; ++i) {
         rdct_status st = validate_plane(&planes[i], "rdct_sweep");
         if (st) return st;
         nchunks += sweep_chunk_count(planes[i]);
+        ntiles += sweep_tiles_of(planes[i]);
     }
-    if (nchunks > INT32_MAX) return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep: too many strips in one call");
+    if (nchunks > INT32_MAX || ntiles > INT32_MAX)
+        return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep: too many strips in one call");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t jb = ((size_t)n * sizeof(JobDesc) + 255) & ~(size_t)255, cb = (size_t)nchunks * sizeof(Chunk);
     void *tables = nullptr;
@@ -274,8 +281,8 @@ rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, doub
         return set_error(RDCT_ERR_OOM, "rdct_sweep: table allocation failed");
     JobDesc *jd = reinterpret_cast<JobDesc *>(tables);
     Chunk *cd = reinterpret_cast<Chunk *>(reinterpret_cast<char *>(tables) + jb);
-    cudaError_t e = build_sweep_tables(planes, n, jd, cd, sse_by_r, s);
-    if (e == cudaSuccess) e = launch_sweep(jd, cd, (int32_t)nchunks, (int)kind, sse_by_r, n, s);
+    cudaError_t e = build_sweep_tables(planes, n, sweep_is_tiled((int)kind), jd, cd, sse_by_r, s);
+    if (e == cudaSuccess) e = launch_sweep(jd, cd, (int32_t)nchunks, (int)kind, sse_by_r, n, (int32_t)ntiles, s);
     if (e == cudaSuccess) e = launch_sweep_finalize(sse_by_r, n, (int)kind, s);
     cudaError_t e2 = cudaFreeAsync(tables, s);
     if (e != cudaSuccess) return cuda_error(e, "rdct_sweep");

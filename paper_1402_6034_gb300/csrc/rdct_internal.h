@@ -160,20 +160,33 @@ unsigned int take_tma_timeouts_r15();
 // nullptr), and of n uint64 squared errors of 8-bit reconstructions in slots8
 // (if not nullptr) to double.
 cudaError_t launch_sse576_to_double(void *slots, int32_t n, cudaStream_t s, void *slots8 = nullptr);
-// Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  Chunks are
-// runs of at most kSweepChunkStrips strips of kFusedVRows block rows.
+// Sweep: per-plane zigzag energy, then suffix sums into SSE(r).  The RDCT
+// pass runs over chunks: runs of at most kSweepChunkStrips strips of
+// kFusedVRows block rows.
 constexpr int kSweepChunkStrips = 8;
-cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
-                          cudaStream_t s);
+cudaError_t launch_sweep2(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, double *out, cudaStream_t s);
 // Sweep tables built on the device from plane descriptors passed as kernel
-// parameters (batches of kSweepBuildBatch planes; no host-to-device copy).
+// parameters (batches of kSweepBuildBatch planes; no host-to-device copy):
+// the jobs and the chunks of the per-block pass, or with `tiles` the jobs of
+// the tiled pass alone (each with its first tile).
 constexpr int kSweepBuildBatch = 1024;
 int64_t sweep_chunk_count(const rdct_plane &p);
 // (also clears out: the planes' 64 bins each)
-cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, JobDesc *jobs, Chunk *chunks, double *out,
-                               cudaStream_t s);
+cudaError_t build_sweep_tables(const rdct_plane *planes, int32_t n, bool tiles, JobDesc *jobs, Chunk *chunks,
+                               double *out, cudaStream_t s);
+// whether the sweep of this kind runs tiled (the DCT pass on the tensor cores)
+inline bool sweep_is_tiled(int kind) { return kind == RDCT_KIND_DCT; }
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
-                         int32_t nplanes, cudaStream_t s);
+                         int32_t nplanes, int32_t ntiles, cudaStream_t s);
+// The DCT pass of the sweep on the tensor cores (rdct_sweep_tc.cu): tiles of
+// 128 blocks of one plane, JobDesc::pad = the plane's first tile.
+constexpr int kSweepTileBlocks = 128;
+__host__ __device__ inline int64_t sweep_tiles_of(const rdct_plane &p) {
+    return ((int64_t)(p.w / 8) * (p.h / 8) + kSweepTileBlocks - 1) / kSweepTileBlocks;
+}
+cudaError_t launch_sweep_dct_tc(const JobDesc *jobs, int32_t nplanes, int32_t total_tiles, double *out,
+                                cudaStream_t s);
+unsigned int take_sweep_tc_timeouts();
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s);
 // 2-D copy of w bytes by h rows done by a kernel (for pageable host memory the
 // device addresses through the host page tables).

@@ -507,10 +507,14 @@ cudaError_t launch_copy2d(void *dst, int64_t dpitch, const void *src, int64_t sp
 }
 
 cudaError_t launch_sweep(const JobDesc *jobs, const Chunk *chunks, int32_t nchunks, int kind, double *out,
-                         int32_t nplanes, cudaStream_t s) {
-    (void)nplanes;
-    if (nchunks <= 0) return cudaSuccess;
-    return launch_sweep2(jobs, chunks, nchunks, kind, out, s);
+                         int32_t nplanes, int32_t ntiles, cudaStream_t s) {
+    // RDCT: the per-block kernel over the chunks; the exact DCT: the tensor-core kernel over the tiles
+    if (!sweep_is_tiled(kind)) {
+        if (nchunks <= 0) return cudaSuccess;
+        return launch_sweep2(jobs, chunks, nchunks, out, s);
+    }
+    if (ntiles <= 0) return cudaSuccess;
+    return launch_sweep_dct_tc(jobs, nplanes, ntiles, out, s);
 }
 
 cudaError_t launch_sweep_finalize(double *out, int32_t nplanes, int kind, cudaStream_t s) {

@@ -74,11 +74,12 @@ extern "C" rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, r
     if (n > kNoAllocMaxPlanes)
         return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: more than 2048 planes in one call; split the call "
                                              "or use rdct_sweep");
-    int64_t nchunks = 0;
+    int64_t nchunks = 0, ntiles = 0;
     for (int32_t i = 0; i < n; ++i) {
         rdct_status st = validate_plane(&planes[i], "rdct_sweep_noalloc");
         if (st) return st;
         nchunks += sweep_chunk_count(planes[i]);
+        ntiles += sweep_tiles_of(planes[i]);
     }
     if (nchunks > kNoAllocMaxChunks)
         return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep_noalloc: the planes need more than 32768 chunks of 512 "
@@ -92,8 +93,8 @@ extern "C" rdct_status rdct_sweep_noalloc(const rdct_plane *planes, int32_t n, r
     cudaStream_t s = (cudaStream_t)stream;
     // the tables are rewritten in full by every call (from plane descriptors
     // passed as kernel parameters), and the same kernel clears the output bins
-    RDCT_CUDA_TRY(build_sweep_tables(planes, n, d_jobs, d_chunks, sse_by_r, s));
-    RDCT_CUDA_TRY(launch_sweep(d_jobs, d_chunks, (int32_t)nchunks, (int)kind, sse_by_r, n, s));
+    RDCT_CUDA_TRY(build_sweep_tables(planes, n, sweep_is_tiled((int)kind), d_jobs, d_chunks, sse_by_r, s));
+    RDCT_CUDA_TRY(launch_sweep(d_jobs, d_chunks, (int32_t)nchunks, (int)kind, sse_by_r, n, (int32_t)ntiles, s));
     RDCT_CUDA_TRY(launch_sweep_finalize(sse_by_r, n, (int)kind, s));
     return RDCT_OK;
 }
