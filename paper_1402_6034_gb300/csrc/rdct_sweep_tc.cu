@@ -9,10 +9,12 @@
 // 64 pixels into the 64 coefficients (row q = 8 i + j: the entries
 // C[i][y] C[j][x]), so D[b][q] = Y_q of block b.  Each thread owns one block:
 // it writes the block's pixels as FP16 straight into its own lane of tensor
-// memory (tcgen05.st; the A operand of tcgen05.mma may live there), one thread
-// issues the MMAs with B from shared memory, and each thread reads its own
-// block's 64 coefficients back (tcgen05.ld) and adds their squares into its
-// energy bins.  No pixel passes through shared memory.
+// memory (tcgen05.st; the A operand of tcgen05.mma may live there), and one
+// thread issues the MMAs with B from shared memory.  The coefficients come
+// back in the 16x256b fragment of tcgen05.ld: lane l of a warp holds
+// columns 8k + 2(l mod 4) + {0, 1} of rows l/4 and l/4 + 8 of each 16-row
+// half of the warp's 32 rows, so each thread keeps 16 energy bins (for
+// four blocks) instead of 64.  No pixel passes through shared memory.
 //
 // The pixels enter centred, a - 128 (exact in FP16; every AC row of C (x) C
 // sums to zero, so the AC coefficients do not change, and the DC coefficient
@@ -45,7 +47,7 @@ namespace {
 constexpr int kTcGroup = 128;             // threads of a group: one block each; 128 blocks per tile = the MMA's M
 constexpr int kTcGroups = 4;              // groups per CTA (one CTA per SM)
 constexpr int kTcThreads = kTcGroup * kTcGroups;
-constexpr int kTcFlushTiles = 64;         // tiles summed in FP32 per thread before the FP64 plane bins
+constexpr int kTcFlushTiles = 32;         // tiles (4 blocks each) summed in FP32 per bin before the FP64 plane bins
 constexpr uint32_t kTcGroupCols = 128;    // tensor memory per group: A in columns 0..31, D in 64..127
 constexpr uint32_t kTcCols = kTcGroupCols * kTcGroups;
 constexpr uint32_t kLbo = 128, kSbo = 8 * 128;  // B: 8 x 16-byte core matrices, K-adjacent 128 B, row groups 1 KB
@@ -147,14 +149,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&a)[16
         "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15])
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
 // Pixels (x, x + 1) of a row word as an FP16 pair a - 128: the byte under the
 // FP16 exponent of 1024 (0x64 high byte), minus 1152 -- exact.
 __device__ __forceinline__ uint32_t px_pair(uint32_t word, int x) {
@@ -165,22 +159,38 @@ __device__ __forceinline__ uint32_t px_pair(uint32_t word, int x) {
     return d;
 }
 
-// The warp's 63 AC bins into the plane's zigzag bins (each lane ends with the
-// totals of bins l and 32 + l and adds them with two atomics).
-__device__ __forceinline__ void tc_flush(double *plane_bins, float (&fb)[64], int lane) {
-    float f0 = 0.0f, f1 = 0.0f;
+__device__ __forceinline__ void tmem_ld_frag(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// The warp's bins into the plane's zigzag bins.  Bin 2k + e of lane l holds
+// coefficient (k, 2(l mod 4) + e); its total is the sum over the eight lanes
+// with the same l mod 4, and lane l adds the totals of row k = l/4: two
+// atomics per lane, the 64 positions of the block once each (DC skipped).
+__device__ __forceinline__ void tc_flush(double *plane_bins, float (&fb)[16], int lane) {
+    const int c = lane & 3, kl = lane >> 2;
+    float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
-    for (int p = 1; p < 64; ++p) {
-        const float s = warp_sum_f32(fb[p]);
-        if (lane == (p & 31)) {
-            if (p < 32) f0 = s;
-            else f1 = s;
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            float v = fb[2 * k + e];
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            if (k == kl) {
+                if (e == 0) s0 = v;
+                else s1 = v;
+            }
+            fb[2 * k + e] = 0.0f;
         }
-        fb[p] = 0.0f;
     }
-    const int k0 = zz_rank(lane >> 3, lane & 7), k1 = zz_rank((32 + lane) >> 3, lane & 7);
-    if (f0 != 0.0f) atomicAdd(plane_bins + k0, (double)f0);
-    if (f1 != 0.0f) atomicAdd(plane_bins + k1, (double)f1);
+    if (s0 != 0.0f && (kl | c) != 0) atomicAdd(plane_bins + zz_rank(kl, 2 * c), (double)s0);
+    if (s1 != 0.0f) atomicAdd(plane_bins + zz_rank(kl, 2 * c + 1), (double)s1);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -233,9 +243,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool failed = false;
     int last_issued = -1;  // tiles of this group whose MMAs were issued: t0 .. last_issued
     if (t0 < t1) {
-        float fb[64];
+        float fb[16];
 #pragma unroll
-        for (int p = 0; p < 64; ++p) fb[p] = 0.0f;
+        for (int p = 0; p < 16; ++p) fb[p] = 0.0f;
         TcPlane cur{};
         {
             int lo = 0, hi = nplanes - 1;
@@ -303,18 +313,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // this block's 64 coefficients: squares into the bins (the DC position is skipped)
+            // the coefficients of four blocks (rows l/4, l/4 + 8 of each 16-row half), 16 positions each:
+            // squares into the bins (the DC squares land in bin 0 of lanes l mod 4 = 0 and are not flushed)
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                uint32_t r[16];
-                tmem_ld16(my_lane + 64u + 16u * h, r);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int half = 0; half < 2; ++half) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int q = 16 * h + c;
-                    if (q == 0) continue;
-                    const float y = __uint_as_float(r[c]);
-                    fb[q] = __fmaf_rn(y, y, fb[q]);
+                for (int kh = 0; kh < 2; ++kh) {
+                    uint32_t r[16];  // r[4 kk + 2 row + e]: column 8 (4 kh + kk) + 2 (l mod 4) + e
+                    tmem_ld_frag(my_lane + ((uint32_t)(16 * half) << 16) + 64u + 32u * (uint32_t)kh, r);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                        for (int row = 0; row < 2; ++row)
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float y = __uint_as_float(r[4 * kk + 2 * row + e]);
+                                float &b = fb[2 * (4 * kh + kk) + e];
+                                b = __fmaf_rn(y, y, b);
+                            }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
