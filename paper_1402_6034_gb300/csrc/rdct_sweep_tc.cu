@@ -16,6 +16,15 @@
 // half of the warp's 32 rows, so each thread keeps 16 energy bins (for
 // four blocks) instead of 64.  No pixel passes through shared memory.
 //
+// The time goes to the chain of each tile (stores into tensor memory, group
+// barrier, MMAs, their commit, loads back): on the 1024 x 512^2 batch, with
+// one wait per load back (92 us per call), copies of the kernel without its
+// global loads took 78 us, without its MMAs (and the wait for them) 65,
+// without both 47.  Overlapping one tile's MMAs with the
+// previous tile's read-back needs two D buffers per group, and so fewer
+// groups (three, 98 us) or A in shared memory (94 us); deeper load prefetch,
+// in registers or through a cp.async ring, was slower as well (100-115 us).
+//
 // The pixels enter centred, a - 128 (exact in FP16; every AC row of C (x) C
 // sums to zero, so the AC coefficients do not change, and the DC coefficient
 // is never needed: every r keeps it).  C (x) C enters as the sum of two FP16
@@ -313,26 +322,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // the coefficients of four blocks (rows l/4, l/4 + 8 of each 16-row half), 16 positions each:
-            // squares into the bins (the DC squares land in bin 0 of lanes l mod 4 = 0 and are not flushed)
+            // the coefficients of four blocks (rows l/4, l/4 + 8 of each 16-row half), 16 positions each,
+            // in four loads and one wait: squares into the bins (the DC squares land in bin 0 of lanes
+            // l mod 4 = 0 and are not flushed)
+            {
+                uint32_t r[4][16];  // r[2 half + kh][4 kk + 2 row + e]: column 8 (4 kh + kk) + 2 (l mod 4) + e
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
+                for (int half = 0; half < 2; ++half)
 #pragma unroll
-                for (int kh = 0; kh < 2; ++kh) {
-                    uint32_t r[16];  // r[4 kk + 2 row + e]: column 8 (4 kh + kk) + 2 (l mod 4) + e
-                    tmem_ld_frag(my_lane + ((uint32_t)(16 * half) << 16) + 64u + 32u * (uint32_t)kh, r);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    for (int kh = 0; kh < 2; ++kh)
+                        tmem_ld_frag(my_lane + ((uint32_t)(16 * half) << 16) + 64u + 32u * (uint32_t)kh, r[2 * half + kh]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int half = 0; half < 2; ++half)
+#pragma unroll
+                for (int kh = 0; kh < 2; ++kh)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
                         for (int row = 0; row < 2; ++row)
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
-                                const float y = __uint_as_float(r[4 * kk + 2 * row + e]);
+                                const float y = __uint_as_float(r[2 * half + kh][4 * kk + 2 * row + e]);
                                 float &b = fb[2 * (4 * kh + kk) + e];
                                 b = __fmaf_rn(y, y, b);
                             }
-                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             // flush at the end of the plane (for this group) or after kTcFlushTiles tiles
