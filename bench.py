@@ -480,13 +480,15 @@ def bench_sweep(args, dev):
     del plan10, rec
     return {"metric": METRIC, "value": total / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32+fp32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "int32 (RDCT) + f16 MMA, f32 accumulate (DCT)", "data": "synthetic",
             "config": {"workload": "sweep_1024x512x512_r1-64_rdct_and_dct", "images": n,
                        "samples_per_step": total, "note": "one pass per transform, 1 B/px read"},
             "roofline": {"bound": "hbm", "achieved": total / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": total / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": f"{kind} hbm_gbs",
-                         "limiter": "instruction issue, not DRAM: both passes need all 63 AC coefficients of "
-                                    "every block (ncu: 63-66 % of issue slots busy, DRAM read 3.0 and 1.9 TB/s)"},
+                         "limiter": "not DRAM: both passes need all 63 AC coefficients of every block. RDCT pass "
+                                    "(per-block kernel) issue-bound, 63 % of issue slots busy, DRAM read 2.9 TB/s; "
+                                    "DCT pass (tensor cores) bound by each tile's chain of tensor-memory stores, "
+                                    "MMAs and loads back, tensor pipe 38 % busy, DRAM read 3.3 TB/s"},
             "gpu_launches": 6 * args.steps, "per_r": rows, "fused_r10_batch": fused10,
             "uqi_kernel": {"image": "512x512 u8", "us": uqi_ms * 1e3,
                            "windows_per_s": 505 * 505 / (uqi_ms / 1e3), "uqi_subset_images": n_uqi}}
