@@ -101,9 +101,10 @@ RDCT_API size_t rdct_last_error(char *buf, size_t cap);
 RDCT_API int32_t rdct_version(void);
 /* Blocks the host until all work on `stream` is done; reports async errors
  * (RDCT_ERR_CUDA).  Returns RDCT_ERR_TIMEOUT when a TMA-staged batch kernel
- * gave up waiting for a staged tile since the last check (its warp stopped
- * early, so that launch's outputs and errors are incomplete); the count is
- * reset by the check.  A staged tile that never arrived in time may still
+ * gave up waiting for a staged tile, or the tensor-core sweep pass for its
+ * MMAs, since the last check (that warp or group stopped early, so that
+ * launch's outputs and errors are incomplete); the counts are reset by the
+ * check.  A staged tile that never arrived in time may still
  * land later in shared memory that another kernel then owns, so after a
  * timeout treat the results of every launch that ran at the same time as
  * suspect too. */
@@ -215,7 +216,13 @@ RDCT_API rdct_status rdct_fused(const rdct_plane *src, int32_t r, rdct_kind kind
  * doubles) receives, for each plane i and r = 1..64, the squared error of
  * the reconstruction keeping r coefficients, computed from the per-zigzag-
  * position energy of the orthonormal coefficients (Parseval: the transform
- * is orthogonal).  Exact for kind RDCT; FP32 products, FP64 sums for DCT. */
+ * is orthogonal).  Exact for kind RDCT (integer transform and energies).  For
+ * kind DCT the coefficients of 128 blocks at a time come from one tensor-core
+ * product: the pixels exactly in FP16, C (x) C as the sum of two FP16 parts,
+ * FP32 accumulation; FP32 sums per thread, FP64 sums per plane.  The
+ * tensor-core pass waits for its MMAs with a bound; a wait that ran out is
+ * reported by rdct_sync (RDCT_ERR_TIMEOUT: those planes' rows are
+ * incomplete). */
 RDCT_API rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, double *sse_by_r, rdct_stream stream);
 
 /* rdct_sweep without any allocation.  The paper has no counterpart: this is a
