@@ -42,52 +42,21 @@
 // tile's MMAs.  (With one 128-thread CTA per group the block scheduler kept
 // fewer groups per SM busy than their resources allow.)
 #include <cuda_runtime.h>
-#include <cuda_fp16.h>
 
 #include <cstdint>
 
 #include "rdct_blocks.cuh"
 #include "rdct_device.cuh"
 #include "rdct_internal.h"
+#include "rdct_tc.cuh"
 
 namespace rdct {
 namespace {
 
-constexpr int kTcGroup = 128;             // threads of a group: one block each; 128 blocks per tile = the MMA's M
-constexpr int kTcGroups = 4;              // groups per CTA (one CTA per SM)
-constexpr int kTcThreads = kTcGroup * kTcGroups;
-constexpr int kTcFlushTiles = 32;         // tiles (4 blocks each) summed in FP32 per bin before the FP64 plane bins
-constexpr uint32_t kTcGroupCols = 128;    // tensor memory per group: A in columns 0..31, D in 64..127
-constexpr uint32_t kTcCols = kTcGroupCols * kTcGroups;
-constexpr uint32_t kLbo = 128, kSbo = 8 * 128;  // B: 8 x 16-byte core matrices, K-adjacent 128 B, row groups 1 KB
-constexpr uint32_t kBBytes = 64 * 64 * 2;
-constexpr int kWaitPolls = 1 << 22;
+using tc::kGroup;
+constexpr int kTcFlushTiles = 32;  // tiles (4 blocks each) summed in FP32 per bin before the FP64 plane bins
 
 __device__ unsigned int g_sweep_tc_timeouts = 0;
-
-__device__ __forceinline__ uint64_t b_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((kSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-// Byte offset of B's element (row n, column k) in the K-major core layout.
-__device__ __forceinline__ uint32_t b_off(int n, int k) {
-    return (uint32_t)((n >> 3) * kSbo + (k >> 3) * kLbo + (n & 7) * 16 + (k & 7) * 2);
-}
-
-// Barrier of the 128 threads of group g (named barrier 1 + g).
-__device__ __forceinline__ void group_sync(int g) {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(kTcGroup) : "memory");
-}
-__device__ __forceinline__ bool group_sync_or(int g, bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(1 + g), "n"(kTcGroup)
-        : "memory");
-    return r != 0;
-}
 
 struct TcPlane {
     int idx, base, end;  // plane index, its first tile, one past its last
@@ -121,11 +90,11 @@ struct TcCursor {
     int by, bx, sq, sr;  // block position; 128 / nbw, 128 mod nbw
 };
 __device__ __forceinline__ void tc_cursor_init(TcCursor &c, int u, int gt) {
-    const int b = (u - c.p.base) * kTcGroup + gt;
+    const int b = (u - c.p.base) * kGroup + gt;
     c.by = b / c.p.nbw;
     c.bx = b - c.by * c.p.nbw;
-    c.sq = kTcGroup / c.p.nbw;
-    c.sr = kTcGroup - c.sq * c.p.nbw;
+    c.sq = kGroup / c.p.nbw;
+    c.sr = kGroup - c.sq * c.p.nbw;
 }
 __device__ __forceinline__ void tc_cursor_next(const JobDesc *jobs, int n, int total, int u, int gt, TcCursor &c) {
     if (u >= c.p.end) {
@@ -148,32 +117,6 @@ __device__ __forceinline__ void tc_load(const TcCursor &c, uint32_t fill, uint32
 #pragma unroll
         for (int i = 0; i < 16; ++i) w[i] = fill;
     }
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&a)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]),
-        "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15])
-        : "memory");
-}
-// Pixels (x, x + 1) of a row word as an FP16 pair a - 128: the byte under the
-// FP16 exponent of 1024 (0x64 high byte), minus 1152 -- exact.
-__device__ __forceinline__ uint32_t px_pair(uint32_t word, int x) {
-    const unsigned b = (unsigned)(x & 3);
-    const uint32_t t = __byte_perm(word, 0x64646464u, b | (4u << 4) | ((b + 1u) << 8) | (4u << 12));
-    uint32_t d;
-    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(t), "r"(0x64806480u));
-    return d;
-}
-
-__device__ __forceinline__ void tmem_ld_frag(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
 }
 
 // The warp's bins into the plane's zigzag bins.  Bin 2k + e of lane l holds
@@ -202,51 +145,34 @@ __device__ __forceinline__ void tc_flush(double *plane_bins, float (&fb)[16], in
     if (s1 != 0.0f) atomicAdd(plane_bins + zz_rank(kl, 2 * c + 1), (double)s1);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(tc::kThreads, 1)
     sweep_dct_tc_kernel(const JobDesc *__restrict__ jobs, int32_t nplanes, int32_t total, double *out,
                         const DctConsts C) {
     constexpr int NB = 2;  // B matrices: the hi and lo parts of C (x) C
-    __shared__ __align__(1024) unsigned char bsm[NB * kBBytes];
-    __shared__ uint64_t bars[kTcGroups];
+    __shared__ __align__(1024) unsigned char bsm[NB * tc::kBBytes];
+    __shared__ uint64_t bars[tc::kGroups];
     __shared__ uint32_t slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = warp >> 2, gt = tid & (kTcGroup - 1);
+    const int g = warp >> 2, gt = tid & (kGroup - 1);
     // this group's tiles [t0, t1)
-    const int64_t ngroups = (int64_t)gridDim.x * kTcGroups, gi = (int64_t)blockIdx.x * kTcGroups + g;
+    const int64_t ngroups = (int64_t)gridDim.x * tc::kGroups, gi = (int64_t)blockIdx.x * tc::kGroups + g;
     const int t0 = (int)(gi * total / ngroups);
     const int t1 = (int)((gi + 1) * total / ngroups);
-    // B: row n = 8 i + j (coefficient), column k = 8 y + x (pixel)
-    for (int e = tid; e < 64 * 64; e += kTcThreads) {
-        const int n = e >> 6, k = e & 63, i = n >> 3, j = n & 7, y = k >> 3, x = k & 7;
-        const float c = C.c[i * 8 + y] * C.c[j * 8 + x];
-        const __half hi = __float2half_rn(c);
-        *reinterpret_cast<__half *>(bsm + b_off(n, k)) = hi;
-        *reinterpret_cast<__half *>(bsm + kBBytes + b_off(n, k)) = __float2half_rn(c - __half2float(hi));
-    }
+    tc::build_kron_b<NB>(bsm, C.c, tid, tc::kThreads);  // row n = 8 i + j (coefficient), column k = 8 y + x (pixel)
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(bsm);
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&bars[g]);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(&slot)),
-                     "r"(kTcCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (gt == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (warp == 0) tc::tmem_alloc_all(&slot);
+    if (gt == 0) tc::mbar_init(mbar);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, written by these threads, is read by the MMAs
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc::fence_after_sync();
     // launched as a programmatic dependent of the table builder (which also
     // clears the bins): the set-up above overlaps the builder's tail
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const uint32_t tb = *reinterpret_cast<volatile uint32_t *>(&slot) + kTcGroupCols * (uint32_t)g;  // this group's columns
+    const uint32_t tb = *reinterpret_cast<volatile uint32_t *>(&slot) + tc::kGroupCols * (uint32_t)g;  // group's columns
     const uint32_t my_lane = tb + ((uint32_t)(32 * (warp & 3)) << 16);
-    // D f32, A and B f16 (A from tensor memory, B K-major), N = 64, M = 128
-    const uint32_t idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
     const uint32_t fill = 0x80808080u;  // a missing block reads as 128 everywhere: zero once centred
 
     bool failed = false;
@@ -272,56 +198,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int since_flush = 0;
         for (int u = t0; u < t1; ++u) {
             tc_plane_seek(jobs, nplanes, total, u, cur);
-            // this thread's block as 64 FP16 values (row y, pixels x, x + 1 in one column) into its lane of A
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t a[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int k = 2 * (16 * h + c), y = k >> 3, x = k & 7;
-                    a[c] = px_pair(w[2 * y + (x >> 2)], x);
-                }
-                tmem_st16(my_lane + 16u * h, a);
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc::store_block_a<128>(my_lane, w);  // this thread's block, centred, into its lane of A
+            tc::tmem_wait_st();
             // the next tile's block: its loads run while this tile is transformed
             if (u + 1 < t1) {
                 tc_cursor_next(jobs, nplanes, total, u + 1, gt, ld);
                 tc_load(ld, fill, w);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            group_sync(g);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t parity = (uint32_t)(u - t0) & 1u;
-            if (gt == 0) {
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-                    for (int m = 0; m < NB; ++m) {
-                        const uint64_t bd = b_desc(sb + (uint32_t)m * kBBytes + (uint32_t)kk * 2u * kLbo);
-                        const uint32_t acc = (kk > 0 || m > 0) ? 1u : 0u;
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tb + 64u),
-                                     "r"(tb + 8u * (uint32_t)kk), "l"(bd), "r"(idesc), "r"(acc));
-                    }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
-            }
+            tc::fence_before_sync();
+            tc::group_sync(g);
+            tc::fence_after_sync();
+            if (gt == 0) tc::mma_tile<NB>(tb + tc::kDCol, tb, sb, mbar);
             last_issued = u;
             // wait (bounded) for the MMAs; a group whose wait runs out stops after this tile
-            uint32_t done = 0;
-            for (int it = 0; it < kWaitPolls && !done; ++it)
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, "
-                    "p;\n\t}"
-                    : "=r"(done)
-                    : "r"(mbar), "r"(parity)
-                    : "memory");
-            if (group_sync_or(g, !done)) {
+            const bool done = tc::mbar_wait(mbar, (uint32_t)(u - t0) & 1u);
+            if (tc::group_sync_or(g, !done)) {
                 failed = true;
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            tc::fence_after_sync();
             // the coefficients of four blocks (rows l/4, l/4 + 8 of each 16-row half), 16 positions each,
             // in four loads and one wait: squares into the bins (the DC squares land in bin 0 of lanes
             // l mod 4 = 0 and are not flushed)
@@ -331,24 +226,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 for (int half = 0; half < 2; ++half)
 #pragma unroll
                     for (int kh = 0; kh < 2; ++kh)
-                        tmem_ld_frag(my_lane + ((uint32_t)(16 * half) << 16) + 64u + 32u * (uint32_t)kh, r[2 * half + kh]);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        tc::tmem_ld_frag(my_lane + ((uint32_t)(16 * half) << 16) + tc::kDCol + 32u * (uint32_t)kh,
+                                         r[2 * half + kh]);
+                tc::tmem_wait_ld();
 #pragma unroll
                 for (int half = 0; half < 2; ++half)
 #pragma unroll
-                for (int kh = 0; kh < 2; ++kh)
+                    for (int kh = 0; kh < 2; ++kh)
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
+                        for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-                        for (int row = 0; row < 2; ++row)
+                            for (int row = 0; row < 2; ++row)
 #pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float y = __uint_as_float(r[2 * half + kh][4 * kk + 2 * row + e]);
-                                float &b = fb[2 * (4 * kh + kk) + e];
-                                b = __fmaf_rn(y, y, b);
-                            }
+                                for (int e = 0; e < 2; ++e) {
+                                    const float y = __uint_as_float(r[2 * half + kh][4 * kk + 2 * row + e]);
+                                    float &b = fb[2 * (4 * kh + kk) + e];
+                                    b = __fmaf_rn(y, y, b);
+                                }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            tc::fence_before_sync();
             // flush at the end of the plane (for this group) or after kTcFlushTiles tiles
             ++since_flush;
             if (u + 1 == t1 || u + 1 >= cur.end || since_flush == kTcFlushTiles) {
@@ -362,23 +258,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (failed) {
         if (gt == 0) atomicAdd(&g_sweep_tc_timeouts, 1u);
         // the MMAs of the tile that timed out may still run: wait (bounded) before releasing the memory
-        const uint32_t parity = (uint32_t)(last_issued - t0) & 1u;
-        uint32_t done = 0;
-        for (int it = 0; it < kWaitPolls && !done; ++it)
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, "
-                "p;\n\t}"
-                : "=r"(done)
-                : "r"(mbar), "r"(parity)
-                : "memory");
+        tc::mbar_test_wait(mbar, (uint32_t)(last_issued - t0) & 1u);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc::fence_before_sync();
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*reinterpret_cast<volatile uint32_t *>(
-                         &slot)),
-                     "r"(kTcCols));
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc_all(*reinterpret_cast<volatile uint32_t *>(&slot));
 }
 
 }  // namespace
@@ -390,10 +275,10 @@ cudaError_t launch_sweep_dct_tc(const JobDesc *jobs, int32_t nplanes, int32_t to
                                 cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
     const int64_t g = sm_count();
-    const int64_t need = (total_tiles + kTcGroups - 1) / kTcGroups;
+    const int64_t need = (total_tiles + tc::kGroups - 1) / tc::kGroups;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(g < need ? g : need));
-    cfg.blockDim = dim3(kTcThreads);
+    cfg.blockDim = dim3(tc::kThreads);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
