@@ -120,10 +120,10 @@ def test_uneven_4096_images(dev):
 def test_plane_larger_than_2gib(dev):
     """One 65536 x 33280 plane (2.18 GB, 35.5 M blocks): byte offsets past 2^31
     in the single-plane kernel, both batch stagings (r = 16 with TMA, r = 10
-    with per-thread copies), the r sweep and the forward transform (whose
+    with per-thread copies), the r sweep of both transforms and the forward transform (whose
     int32 output passes 2^31 elements).  Whole-plane SSE against the oracle,
     three 16-row bands (first rows, the rows that straddle byte 2^31, last
-    rows) element by element."""
+    rows) element by element; the DCT sweep's SSE(16) against the oracle."""
     from paper_1402_6034_gb300 import synth
     h, w = 33280, 65536
     pool = synth.field_u8_torch(2048, 2048, 2.0, 7, device=str(dev), planes=4)
@@ -141,6 +141,7 @@ def test_plane_larger_than_2gib(dev):
     sse_b = torch.empty(2, dtype=torch.float64, device=dev)
     plan.run(sse_b)
     sw = rdct.sweep([img], rdct.KIND_RDCT)
+    sw_d = rdct.sweep([img], rdct.KIND_DCT)  # the tensor-core pass: tiles past byte 2^31
     torch.cuda.synchronize()
     plan.close()
     assert torch.equal(u8, d16), "single-plane and batch (TMA) reconstructions differ"
@@ -153,6 +154,10 @@ def test_plane_larger_than_2gib(dev):
     _, _, so10, _ = orc.fused(host, 10, want_xhat=False, want_u8=False, nthreads=0)
     assert sse.item() == pytest.approx(so16, rel=1e-9)
     assert sse_b[1].item() == pytest.approx(so10, rel=1e-9)
+    _, _, sd16, _ = orc.fused(host, 16, kind=rdct.KIND_DCT, want_xhat=False, want_u8=False, nthreads=0)
+    d_np = sw_d[0].cpu().numpy()
+    assert_sse_close(d_np[15], sd16, host.size)
+    assert np.all(np.diff(d_np) <= 1e-6 * np.maximum(d_np[:-1], 1.0))
     Y = rdct.forward(img)
     torch.cuda.synchronize()
     assert Y.numel() > 2 ** 31

@@ -138,3 +138,16 @@ def test_sweep_dct_tiles_across_planes(dev):
     for i, img in enumerate(imgs):
         _check_against_oracle(o[i], img, rdct.KIND_DCT)
         _same_contents(o[i], rev[i], rdct.KIND_DCT)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_sweep_many_tiny_planes(dev, kind):
+    """2500 planes of 1 to 9 blocks in one call (more planes than the DCT
+    pass has groups of threads, every tile partial): every row against the
+    oracle."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    shapes = [(8 * int(a), 8 * int(b)) for a, b in rng.integers(1, 4, size=(2500, 2))]
+    imgs = [_rng_plane(h, w, 100 + i) for i, (h, w) in enumerate(shapes)]
+    out = rdct.sweep([to_dev(i, dev) for i in imgs], kind).cpu().numpy()
+    for i, img in enumerate(imgs):
+        _check_against_oracle(out[i], img, kind)
