@@ -275,7 +275,9 @@ rdct_status rdct_sweep(const rdct_plane *planes, int32_t n, rdct_kind kind, doub
     if (nchunks > INT32_MAX || ntiles > INT32_MAX)
         return set_error(RDCT_ERR_TOO_LARGE, "rdct_sweep: too many strips in one call");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t jb = ((size_t)n * sizeof(JobDesc) + 255) & ~(size_t)255, cb = (size_t)nchunks * sizeof(Chunk);
+    // (the tiled pass needs the job table alone)
+    const size_t jb = ((size_t)n * sizeof(JobDesc) + 255) & ~(size_t)255,
+                 cb = sweep_is_tiled((int)kind) ? 0 : (size_t)nchunks * sizeof(Chunk);
     void *tables = nullptr;
     if (cudaMallocAsync(&tables, jb + cb, s) != cudaSuccess)
         return set_error(RDCT_ERR_OOM, "rdct_sweep: table allocation failed");
