@@ -20,19 +20,21 @@
 // barrier, MMAs, their commit, loads back): on the 1024 x 512^2 batch, with
 // one wait per load back (92 us per call), copies of the kernel without its
 // global loads took 78 us, without its MMAs (and the wait for them) 65,
-// without both 47.  Overlapping one tile's MMAs with the
-// previous tile's read-back needs two D buffers per group, and so fewer
-// groups (three, 98 us) or A in shared memory (94 us); deeper load prefetch,
-// in registers or through a cp.async ring, was slower as well (100-115 us).
+// without both 47.  Overlapping one tile's MMAs with the previous tile's
+// read-back needs two D buffers per group, and so fewer groups (three,
+// 98 us) or A in shared memory (94 us); deeper load prefetch, in registers
+// or through a cp.async ring, was slower as well (100-115 us), and so was a
+// single thread waiting for the MMAs instead of all (88 us).
 //
 // The pixels enter centred, a - 128 (exact in FP16; every AC row of C (x) C
 // sums to zero, so the AC coefficients do not change, and the DC coefficient
 // is never needed: every r keeps it).  C (x) C enters as the sum of two FP16
 // matrices (hi and lo parts) accumulated into the same FP32 result, which
 // keeps the coefficients at FP32 accuracy; FP32 bins per thread, FP64 plane
-// bins.  (The RDCT pass stays on the per-block kernel: its exact integer
-// squares cost twice the FMAs here, and on the tensor cores it measured
-// 116 us against 102 us per call on 1024 x 512^2.)
+// bins.  (The RDCT pass stays on the per-block kernel: in this form each of
+// its coefficients needs an exact conversion and an integer multiply-add
+// where the DCT needs one FFMA, and it measured 123 us against 102 us per
+// call on 1024 x 512^2.)
 //
 // Work: a flat list of tiles over the planes (JobDesc::pad = the plane's first
 // tile, non-decreasing).  One CTA per SM of four independent groups of 128
