@@ -23,8 +23,9 @@
 // without both 47.  Overlapping one tile's MMAs with the previous tile's
 // read-back needs two D buffers per group, and so fewer groups (three,
 // 98 us) or A in shared memory (94 us); deeper load prefetch, in registers
-// or through a cp.async ring, was slower as well (100-115 us), and so was a
-// single thread waiting for the MMAs instead of all (88 us).
+// or through a cp.async ring, was slower as well (100-115 us), and so were a
+// single thread waiting for the MMAs instead of all (88 us) and six groups
+// per SM with A in shared memory (89 us).
 //
 // The pixels enter centred, a - 128 (exact in FP16; every AC row of C (x) C
 // sums to zero, so the AC coefficients do not change, and the DC coefficient
